@@ -1,0 +1,143 @@
+"""CPU oracle for Strassen-fused GEMM (Huang, Smith, Henry, van de Geijn 2016).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with the
+CUDA library in ``paper_1605_01078_gb300`` and never imports it.
+
+Contents
+--------
+* :func:`gemm`, :func:`strassen`, :func:`gemm_sampled` -- thin numpy wrappers over
+  the plain C in ``oracle.c`` (classical definition, Section 2.1; recursive textbook
+  Strassen per Figure 1, Sections 3.1-3.3; Dot2-compensated sampled entries).
+* :mod:`oracle.tables` -- the one-level table of Figure 1 and the L-level tables of
+  Eq. 4 built as Kronecker powers of it (Sections 3.5-3.6).
+* :mod:`oracle.ozaki` -- error-free splitting of FP64 operands into integer slices
+  and their exact products (split-precision emulation).
+* :mod:`oracle.mlp` -- FP64 forward/backward of the variant-selector MLP.
+* :mod:`oracle.model` -- the analytic time model of Section 4.2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``liboracle.so`` with plain gcc (portable flags only:
+    no -march, no contraction of a*b+c into fma, so that the arithmetic is exactly
+    what the source says on x86_64 and aarch64 alike)."""
+    if force or not os.path.exists(_LIB_PATH) or (
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.oracle_gemm.restype = i64
+        lib.oracle_gemm.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.oracle_strassen.restype = i64
+        lib.oracle_strassen.argtypes = [ctypes.c_int, i64, i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.oracle_gemm_sampled.restype = None
+        lib.oracle_gemm_sampled.argtypes = [i64, dp, i64, dp, i64, dp, i64,
+                                            ctypes.POINTER(i64), ctypes.POINTER(i64), i64, dp]
+        _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check2d(x: np.ndarray, name: str) -> np.ndarray:
+    if x.dtype != np.float64 or x.ndim != 2:
+        raise TypeError(f"{name} must be a 2-D float64 array")
+    if x.strides[1] != 8 or x.strides[0] % 8:
+        raise TypeError(f"{name} must be row-major with unit column stride")
+    return x
+
+
+def gemm(A: np.ndarray, B: np.ndarray, C: np.ndarray) -> int:
+    """In place: C += A @ B by the classical definition (Section 2.1).
+
+    Returns the number of scalar multiplications (m*n*k)."""
+    _check2d(A, "A"); _check2d(B, "B"); _check2d(C, "C")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or C.shape != (m, n):
+        raise ValueError("shape mismatch")
+    r = _load().oracle_gemm(m, n, k, _dp(A), A.strides[0] // 8, _dp(B), B.strides[0] // 8,
+                            _dp(C), C.strides[0] // 8)
+    if r < 0:
+        raise MemoryError("oracle_gemm")
+    return int(r)
+
+
+def strassen(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int) -> int:
+    """In place: C += A @ B by ``levels`` recursive levels of Figure 1 (textbook
+    Strassen with zero padding of odd sizes), classical at the leaves.
+
+    Returns the number of scalar multiplications performed at the leaves
+    (7^L * ceil-halved sizes, against m*n*k for the classical definition)."""
+    _check2d(A, "A"); _check2d(B, "B"); _check2d(C, "C")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or C.shape != (m, n):
+        raise ValueError("shape mismatch")
+    r = _load().oracle_strassen(int(levels), m, n, k, _dp(A), A.strides[0] // 8,
+                                _dp(B), B.strides[0] // 8, _dp(C), C.strides[0] // 8)
+    if r < 0:
+        raise MemoryError("oracle_strassen")
+    return int(r)
+
+
+def gemm_sampled(A: np.ndarray, B: np.ndarray, C0: np.ndarray | None,
+                 rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+    """Entries (rows[t], cols[t]) of C0 + A @ B, each computed with the compensated
+    dot product Dot2 (twice-working-precision accuracy, then rounded)."""
+    _check2d(A, "A"); _check2d(B, "B")
+    m, k = A.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    if rows.shape != cols.shape or rows.ndim != 1:
+        raise ValueError("rows/cols must be 1-D of equal length")
+    if rows.size and (rows.min() < 0 or rows.max() >= m or cols.min() < 0 or cols.max() >= B.shape[1]):
+        raise IndexError("sample index out of range")
+    out = np.empty(rows.size, dtype=np.float64)
+    if C0 is not None:
+        _check2d(C0, "C0")
+        c0p, ldc = _dp(C0), C0.strides[0] // 8
+    else:
+        c0p, ldc = ctypes.cast(None, ctypes.POINTER(ctypes.c_double)), 0
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    _load().oracle_gemm_sampled(k, _dp(A), A.strides[0] // 8, _dp(B), B.strides[0] // 8,
+                                c0p, ldc, rows.ctypes.data_as(P64), cols.ctypes.data_as(P64),
+                                rows.size, _dp(out))
+    return out
+
+
+def max_rel_err(C: np.ndarray, C_ref: np.ndarray, A: np.ndarray, B: np.ndarray) -> float:
+    """Element-wise max-norm error scaled by the operands: max|C - C_ref| /
+    (max|A| * max|B|).  Zero operands give the plain max error."""
+    den = float(np.max(np.abs(A), initial=0.0)) * float(np.max(np.abs(B), initial=0.0))
+    err = float(np.max(np.abs(np.asarray(C) - np.asarray(C_ref)), initial=0.0))
+    return err / den if den > 0 else err
+
+
+__all__ = ["build", "gemm", "strassen", "gemm_sampled", "max_rel_err"]
