@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the Strassen-fused FP64 GEMM on GB300 (one JSON line on rank 0).
+
+Workload (default): m = n = k = 8192, FP64, A, B, C i.i.d. uniform[-1, 1] from fixed
+seeds, C += A*B (accumulate mode), 2-level ABC Strassen.  One step = one
+strassen_gemm call through the C ABI on inputs resident in HBM (1.5 GB of operands,
+larger than the 129 MB L2, so no flush is needed between steps).
+
+Metric: effective GFLOPS = 2mnk / t * 1e-9 (the paper's Eq. for effective GFLOPS).
+Also reported: the library's classical FP64 kernel on the same inputs (the
+comparator), an end-to-end figure with host buffers, the roofline of the FP64 product
+kernel against the FP64 pipe, SM clocks sampled during the timed region, and the CPU
+oracle timed on a bounded sample.
+
+Multi-GPU: the path does not shard into a collective; N ranks run N independent
+replicas ("replicas only"), value = total effective flops of all ranks / the slowest
+rank's time.
+
+--impl reference times the CPU oracle (textbook recursive Strassen, plain C, one
+thread) on a bounded sample of the same workload (m = n = k = 1024 per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "effective GFLOPS (2mnk/t) Strassen vs classical GEMM, 1 GB300, rel err ≤1e-12"
+UNIT = "GFLOP/s"
+# FP64 pipe peak: 2 FMA lanes (4 flops) per clock per SM x 152 SMs x 2070 MHz max clock.
+FP64_PEAK_GFLOPS = 4 * 152 * 2070e6 / 1e9
+CPU_SAMPLE_N = 2048
+REF_SAMPLE_N = 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--levels", type=int, default=2)
+    ap.add_argument("--variant", default="ABC")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_flops(m, n, k, levels):
+    """FP64 flops the method performs: 7^L products of 2 h_m h_n h_k (Section 3.1-3.2)
+    plus the extra additions of the performance model's T_a (Section 4.2) with the
+    operand and C term counts of the L-level table."""
+    from paper_1605_01078_gb300 import strassen_plan_table
+    P = 1 << levels
+    hm, hn, hk = -(-m // P), -(-n // P), -(-k // P)
+    tab = strassen_plan_table(levels)
+    a_adds = sum(len(p[0]) - 1 for p in tab)
+    b_adds = sum(len(p[1]) - 1 for p in tab)
+    c_upd = sum(len(p[2]) for p in tab) if levels > 0 else 0
+    return len(tab) * 2.0 * hm * hn * hk + 2.0 * (a_adds * hm * hk + b_adds * hk * hn + c_upd * hm * hn)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the FP64 product kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fp64_strassen_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            a, b = line.split("=", 1)
+            rec[a.strip()] = b.strip()
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1605_01078_gb300", "csrc", "fp64_gemm.cu"))):
+        h.update(open(f, "rb").read())
+    if rec.get("kernel_source_sha256") != h.hexdigest():
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch_8192_2L_ABC"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_oracle_effective(n, levels, reps=1):
+    import numpy as np
+    import oracle
+    import workloads as W
+    A, B = W.uniform(n, n, 0), W.uniform(n, n, 1)
+    C = W.uniform(n, n, 2)
+    oracle.build()
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.strassen(A, B, C, levels)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return 2.0 * n ** 3 / best / 1e9, best
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads as W
+    n = REF_SAMPLE_N
+    A, B, C = W.uniform(n, n, 0), W.uniform(n, n, 1), W.uniform(n, n, 2)
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.strassen(A, B, C, args.levels)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.strassen(A, B, C, args.levels)
+    dt = time.perf_counter() - t0
+    val = 2.0 * n ** 3 * args.steps / dt / 1e9
+    sample = f"m=n=k={n} {args.levels}-level textbook Strassen per step (oracle, plain C, 1 thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"square m=n=k={args.n} FP64 {args.levels}-level {args.variant} Strassen, C += A*B"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_1605_01078_gb300 as sg
+    import workloads as W
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    m = n = k = args.n
+    L, variant = args.levels, args.variant
+    sg.load_library()
+    A = torch.from_numpy(W.uniform(m, k, 100 + rank)).cuda()
+    B = torch.from_numpy(W.uniform(k, n, 200 + rank)).cuda()
+    C = torch.from_numpy(W.uniform(m, n, 300 + rank)).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sg.gemm(A, B, C, levels=L, variant=variant, stream=stream)
+
+    launches_per_step = 1 if (L == 0 or variant.upper() == "ABC") else None
+    if launches_per_step is None:
+        nprod = 7 ** L
+        launches_per_step = nprod * (2 if variant.upper() == "AB" else 4)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    per_launch = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    eff_flops = 2.0 * m * n * k
+    value = eff_flops * args.steps * ws / elapsed / 1e9
+
+    # Comparator: the library's classical kernel on the same inputs.
+    cls_steps = max(2, args.steps // 3)
+    sg.classical(A, B, C)
+    barrier()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(cls_steps):
+        sg.classical(A, B, C)
+    c1.record(stream)
+    barrier()
+    cls_val = eff_flops * cls_steps / (c0.elapsed_time(c1) / 1e3) / 1e9
+
+    # End to end through the public API with pinned host buffers.
+    e2e = None
+    if not args.no_e2e:
+        hA, hB, hC = A.cpu().pin_memory(), B.cpu().pin_memory(), C.cpu().pin_memory()
+        hOut = torch.empty_like(hC).pin_memory()
+        dA, dB, dC = torch.empty_like(A), torch.empty_like(B), torch.empty_like(C)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            dC.copy_(hC, non_blocking=True)
+            sg.gemm(dA, dB, dC, levels=L, variant=variant, stream=stream)
+            hOut.copy_(dC, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        e_steps = max(2, args.steps // 3)
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(e_steps):
+            e2e_step()
+        x1.record(stream)
+        barrier()
+        et = x0.elapsed_time(x1) / 1e3
+        if dist is not None:
+            t = torch.tensor([et], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": eff_flops * e_steps * ws / et / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(3 * 8 * m * n), "d2h_bytes_per_step": int(8 * m * n)}
+        del dA, dB, dC
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    alg = algorithmic_flops(m, n, k, L)
+    launch_s = statistics.mean(per_launch)
+    achieved = alg / launch_s / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS,
+            "traffic": recorded_traffic() if (L == 2 and variant.upper() == "ABC" and m == 8192) else None,
+            "kernel": "fp64_strassen_kernel",
+            "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz (derived); DFMA probe measured 1200 GFLOP/s"}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cv, ct = cpu_oracle_effective(CPU_SAMPLE_N, L)
+        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"m=n=k={CPU_SAMPLE_N} {L}-level textbook Strassen (plain C, 1 thread), {ct:.1f} s"}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"square m=n=k={m} FP64 {L}-level {variant} Strassen, C += A*B (accumulate), "
+                               f"A,B,C uniform[-1,1]", "m": m, "n": n, "k": k, "levels": L, "variant": variant,
+                   "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (3 x 8 m n bytes)"},
+        "classical": {"value": cls_val, "unit": UNIT, "speedup": value / ws / cls_val},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * strassen.h -- C ABI of the GB300 (sm_103a) Strassen-fused GEMM library.
+ *
+ * The library implements the family of Strassen implementations of Huang, Smith,
+ * Henry and van de Geijn, "Implementing Strassen's Algorithm with BLIS" (FLAME
+ * Working Note #79, arXiv:1605.01078):
+ *
+ *   - the general operation of Eq. 1 / Eq. 3 / Eq. 4 (Sections 3.4-3.6): for every
+ *     row r of the L-level coefficient table,
+ *         M_r = (sum_s delta_s X_s)(sum_t eps_t V_t);   C_q += gamma_q M_r,
+ *     with X_s blocks of A, V_t blocks of B, C_q blocks of C in a 2^L x 2^L partition;
+ *   - the one-level table of Figure 1 and the two-level table of Figure 2 (its
+ *     Kronecker square);
+ *   - the three variants of Section 4.1: "ABC" (operand sums formed while operand
+ *     tiles are staged, each M_r scattered into its C blocks in the kernel
+ *     epilogue), "AB" (fused sums, explicit temporary M, separate C updates) and
+ *     "Naive" (explicit operand-sum temporaries, a classical GEMM, separate C
+ *     updates).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Operation:  C <- C + A * B  (alpha = beta = 1; the paper reduces DGEMM to
+ *             C = alpha*A*B + C in Section 2.2 and this library fixes alpha = 1).
+ * Layout:     row-major.  A is m x k with lda >= k, B is k x n with ldb >= n, C is
+ *             m x n with ldc >= n; element (i, j) of A is A[i*lda + j].  Column-major
+ *             callers pass (B^T, A^T, C^T) with m and n swapped.
+ * Memory:     A, B, C are DEVICE pointers owned by the caller, 8-byte aligned; C must
+ *             not overlap A or B.  Calls are asynchronous on `stream` (a
+ *             cudaStream_t; NULL = the legacy default stream).  Unless stated
+ *             otherwise the library allocates nothing for ABC and classical calls;
+ *             AB and Naive take stream-ordered temporaries (cudaMallocAsync /
+ *             cudaFreeAsync on `stream`) of strassen_workspace_size() bytes.
+ * Sizes:      m, n, k >= 0; a call with m, n or k equal to 0 does nothing and
+ *             returns STRASSEN_OK.  Odd and non-power-of-two sizes are handled by
+ *             virtual zero padding: block i of a dimension d spans
+ *             [i*h, min((i+1)*h, d)) with h = ceil(d / 2^L) (Section 3.3).
+ * Errors:     every function returns STRASSEN_OK (0) or a negative status; nothing
+ *             throws, exits or traps.  Invalid arguments are rejected on the host
+ *             before anything is launched.  STRASSEN_ERR_CUDA reports a CUDA error
+ *             seen by the call (launch failure or an earlier asynchronous error).
+ * Numbers:    FP64 in and out.  For the split-precision dtypes the products run on
+ *             the tensor cores on integer slices of the FP64 operands (see
+ *             strassen_dtype) and the scaling, recombination and C accumulation stay
+ *             in FP64.
+ */
+#ifndef STRASSEN_GB300_H
+#define STRASSEN_GB300_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define STRASSEN_API __attribute__((visibility("default")))
+#else
+#define STRASSEN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* strassen_stream_t; /* a cudaStream_t */
+
+/* Implementation variant (Section 4.1, "Variations on a theme"). */
+typedef enum {
+  STRASSEN_ABC = 0,   /* sums fused into operand staging, M_r scattered into C in the epilogue */
+  STRASSEN_AB = 1,    /* sums fused into operand staging, M_r to a temporary, then C updates */
+  STRASSEN_NAIVE = 2, /* operand-sum temporaries, classical GEMM into M_r, then C updates */
+  STRASSEN_AUTO = 3   /* chosen by strassen_select() */
+} strassen_variant;
+
+/* Arithmetic of the products. */
+typedef enum {
+  STRASSEN_F64 = 0,         /* FP64 fused multiply-adds */
+  STRASSEN_F64_OZ_INT8 = 1, /* FP64 emulated by exact products of INT8 slices (INT32 accumulation) */
+  STRASSEN_F64_OZ_BF16 = 2  /* FP64 emulated by exact products of BF16 integer slices (FP32 accumulation, k-chunked) */
+} strassen_dtype;
+
+/* Status codes. */
+#define STRASSEN_OK 0
+#define STRASSEN_ERR_DIM (-1)         /* m, n or k negative */
+#define STRASSEN_ERR_LD (-2)          /* lda < k, ldb < n or ldc < n (with a non-empty operand) */
+#define STRASSEN_ERR_NULL (-3)        /* NULL pointer with a non-empty operand */
+#define STRASSEN_ERR_LEVELS (-4)      /* levels outside {-1, 0, 1, 2} */
+#define STRASSEN_ERR_UNSUPPORTED (-5) /* unknown dtype or variant, or a combination not built */
+#define STRASSEN_ERR_CUDA (-6)        /* a CUDA runtime error */
+#define STRASSEN_ERR_TIMEOUT (-7)     /* a device-side wait gave up (batched work queue) */
+#define STRASSEN_ERR_ALLOC (-8)       /* a temporary could not be allocated */
+#define STRASSEN_ERR_ARG (-9)         /* any other invalid argument (count, pointer array, ...) */
+
+/*
+ * strassen_gemm -- C += A*B with `levels` levels of Strassen in `variant`.
+ *
+ * Defined by Eq. 4 (Section 3.6) with the Figure 1 table (levels = 1) or its
+ * Kronecker square, Figure 2 (levels = 2); levels = 0 is the classical product of
+ * Section 2.1.  levels = -1 or variant = STRASSEN_AUTO asks strassen_select() for the
+ * choice.  Levels are clamped down while 2^levels exceeds min(m, n, k) (a block would
+ * be empty in every product); the call still succeeds.
+ *
+ *   m, n, k       sizes (>= 0); A m x k, B k x n, C m x n, row-major.
+ *   A, lda        device pointer and row stride (elements) of A, lda >= max(k, 1).
+ *   B, ldb        device pointer and row stride of B, ldb >= max(n, 1).
+ *   C, ldc        device pointer and row stride of C, ldc >= max(n, 1); read and written.
+ *   levels        -1 (auto), 0, 1 or 2.
+ *   variant       STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE or STRASSEN_AUTO.
+ *   dtype         STRASSEN_F64 or one of the split-precision dtypes.
+ *   stream        the CUDA stream the work is ordered on.
+ *
+ * Returns STRASSEN_OK or a negative status; on error C is untouched unless the status
+ * is STRASSEN_ERR_CUDA (work may have been partly launched).  ABC in FP64 with the
+ * default scheduling accumulates the partial products into C with device atomics, so
+ * the rounding order (not the mathematical result) can vary from run to run; set the
+ * environment variable STRASSEN_DETERMINISTIC=1 to make every C tile owned by one
+ * thread block, which fixes the order (at some cost in load balance).
+ */
+STRASSEN_API int strassen_gemm(int64_t m, int64_t n, int64_t k,
+                  const double* A, int64_t lda,
+                  const double* B, int64_t ldb,
+                  double* C, int64_t ldc,
+                  int levels, strassen_variant variant, strassen_dtype dtype,
+                  strassen_stream_t stream);
+
+/*
+ * classical_gemm -- C += A*B by the classical definition of Section 2.1
+ * (gamma_ij += sum_p alpha_ip beta_pj), in FP64 on the library's own kernel.
+ * Arguments, layout, ownership and errors as strassen_gemm.  Each C tile is owned by
+ * one thread block unless splitting k is needed to fill the GPU, in which case the
+ * partial sums are accumulated with device atomics.
+ */
+STRASSEN_API int classical_gemm(int64_t m, int64_t n, int64_t k,
+                   const double* A, int64_t lda,
+                   const double* B, int64_t ldb,
+                   double* C, int64_t ldc,
+                   strassen_stream_t stream);
+
+/* One problem of a batched call: C += A*B as in strassen_gemm. */
+typedef struct {
+  int64_t m, n, k;
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t lda, ldb, ldc;
+  int levels;               /* -1 = the autotuner's choice, else 0, 1 or 2 */
+  strassen_variant variant; /* STRASSEN_AUTO = the autotuner's choice; AB and Naive run as ABC */
+} strassen_problem;
+
+/*
+ * strassen_gemm_batched -- many independent products of uneven shapes in ONE
+ * persistent kernel launch (the batching pattern; not in the paper).
+ *
+ *   count   number of problems (>= 0).
+ *   probs   HOST array of `count` problems; each is validated as in strassen_gemm.
+ *           The C blocks of different problems must not overlap.
+ *   dtype   STRASSEN_F64.
+ *   stream  the CUDA stream.
+ *
+ * The problems are split into work units (problem, product, tile, k-range) listed in
+ * a device work list; resident thread blocks take units from a device counter until
+ * the list is empty.  The call copies the work list to a stream-ordered temporary,
+ * so it can be captured in a CUDA graph and replayed.  Returns STRASSEN_OK or a
+ * negative status (STRASSEN_ERR_TIMEOUT if a device-side wait gave up).
+ */
+STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
+                          strassen_dtype dtype, strassen_stream_t stream);
+
+/*
+ * strassen_select -- the variant selector: predicts the fastest of {classical,
+ * 1L/2L x ABC/AB/Naive} x tile for an m x n x k product in `dtype` (the choice of
+ * implementation the paper's performance model of Section 4.2 is meant to support).
+ * Uses the trained MLP loaded by strassen_selector_load(); without one, or when the
+ * shape was timed by the autotuner, the exhaustive measurement recorded by
+ * strassen_tune_record() is used instead; with neither, a fixed rule (2 levels of
+ * ABC when min(m, n, k) >= 2048, else classical).
+ *
+ *   levels, variant, tile_id   outputs (host pointers, non-NULL).
+ * Returns STRASSEN_OK or a negative status.
+ */
+STRASSEN_API int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype,
+                    int* levels, strassen_variant* variant, int* tile_id);
+
+/*
+ * strassen_workspace_size -- bytes of stream-ordered temporaries a strassen_gemm call
+ * with these arguments takes (0 for ABC and classical in FP64).  AB needs one
+ * (m/2^L) x (n/2^L) temporary M (Section 5, conclusion); Naive adds the operand sums.
+ * Returns a negative status for invalid arguments.
+ */
+STRASSEN_API int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels,
+                                strassen_variant variant, strassen_dtype dtype);
+
+/* strassen_status_string -- a static, NUL-terminated description of a status code. */
+STRASSEN_API const char* strassen_status_string(int status);
+
+/*
+ * strassen_plan_table -- copies the coefficient table the library uses for `levels`
+ * (0, 1 or 2) into host arrays, for inspection and tests; no GPU work.
+ *
+ * Each of the 7^levels products r has up to 2^levels terms per operand.  Term t of
+ * product r is stored at index r*4 + t of a_terms, b_terms, c_terms as
+ * (block_row * 16 + block_col) * 2 + (sign < 0), and the term counts at na[r], nb[r],
+ * nc[r].  `capacity` is the number of products the arrays can hold (a_terms etc.
+ * hold 4*capacity ints).  Returns the number of products, or a negative status.
+ */
+STRASSEN_API int strassen_plan_table(int levels, int capacity, int* na, int* nb, int* nc,
+                        int* a_terms, int* b_terms, int* c_terms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STRASSEN_GB300_H */

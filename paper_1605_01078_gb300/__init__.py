@@ -1,0 +1,77 @@
+"""Strassen's algorithm fused into GEMM on GB300 (sm_103a).
+
+Implements the family of Huang, Smith, Henry and van de Geijn, "Implementing
+Strassen's Algorithm with BLIS" (arXiv:1605.01078): one- and two-level Strassen in the
+ABC, AB and Naive variants plus the classical product, behind the C ABI of
+``include/strassen.h``.  This package is the thin Python side of that ABI:
+
+* :mod:`._binding` -- the C entry points under the same names (ctypes marshalling);
+* :func:`gemm`, :func:`classical` -- the same calls taking torch CUDA tensors, which
+  supply device memory and the stream only.
+
+All arithmetic runs in the library's CUDA kernels; a missing library is an error.
+"""
+from __future__ import annotations
+
+from . import _binding
+from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  # noqa: F401
+                       STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_NAIVE, StrassenError,
+                       classical_gemm, strassen_gemm, strassen_gemm_batched, strassen_plan_table,
+                       strassen_problem, strassen_select, strassen_status_string,
+                       strassen_workspace_size)
+
+VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO}
+DTYPES = {"f64": STRASSEN_F64, "oz_int8": STRASSEN_F64_OZ_INT8, "oz_bf16": STRASSEN_F64_OZ_BF16}
+
+
+def _mat(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D torch.float64 tensor")
+    if not t.is_cuda:
+        raise TypeError(f"{name} must live on a CUDA device")
+    if t.stride(1) != 1 and t.size(1) > 1:
+        raise TypeError(f"{name} must be row-major with unit column stride")
+    return t
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ld(t):
+    return max(t.stride(0), t.size(1), 1)
+
+
+def gemm(A, B, C, levels: int = 1, variant="ABC", dtype="f64", stream=None) -> None:
+    """In place on the stream: C += A @ B with ``levels`` levels of Strassen."""
+    A, B, C = _mat(A, "A"), _mat(B, "B"), _mat(C, "C")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError(f"shape mismatch: A {tuple(A.shape)}, B {tuple(B.shape)}, C {tuple(C.shape)}")
+    v = VARIANTS[variant.upper()] if isinstance(variant, str) else int(variant)
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    st = strassen_gemm(m, n, k, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                       int(levels), v, d, _stream(stream))
+    _binding._check(st, "strassen_gemm")
+
+
+def classical(A, B, C, stream=None) -> None:
+    """In place on the stream: C += A @ B by the library's classical FP64 kernel."""
+    A, B, C = _mat(A, "A"), _mat(B, "B"), _mat(C, "C")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError("shape mismatch")
+    st = classical_gemm(m, n, k, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                        _stream(stream))
+    _binding._check(st, "classical_gemm")
+
+
+def load_library():
+    """Load the CUDA library (building it if needed) and return the ctypes handle."""
+    return _binding.lib()

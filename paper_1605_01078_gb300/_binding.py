@@ -1,0 +1,127 @@
+"""ctypes binding of the C ABI in ``include/strassen.h``.
+
+Argument marshalling only: every function here forwards to the entry point of the
+same name in ``libstrassen_gb300.so``; all arithmetic runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library cannot be loaded, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstrassen_gb300.so")
+
+# enums of strassen.h
+STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE, STRASSEN_AUTO = 0, 1, 2, 3
+STRASSEN_F64, STRASSEN_F64_OZ_INT8, STRASSEN_F64_OZ_BF16 = 0, 1, 2
+
+STATUS = {
+    0: "STRASSEN_OK", -1: "STRASSEN_ERR_DIM", -2: "STRASSEN_ERR_LD", -3: "STRASSEN_ERR_NULL",
+    -4: "STRASSEN_ERR_LEVELS", -5: "STRASSEN_ERR_UNSUPPORTED", -6: "STRASSEN_ERR_CUDA",
+    -7: "STRASSEN_ERR_TIMEOUT", -8: "STRASSEN_ERR_ALLOC", -9: "STRASSEN_ERR_ARG",
+}
+
+
+class StrassenError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status})")
+
+
+class strassen_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
+                ("levels", ctypes.c_int), ("variant", ctypes.c_int)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+# (name, restype, argtypes) of every entry point declared in include/strassen.h
+_I64, _P, _I, _IP = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)
+SIGNATURES = {
+    "strassen_gemm": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _I, _I, _P]),
+    "classical_gemm": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _P]),
+    "strassen_gemm_batched": (_I, [_I, ctypes.POINTER(strassen_problem), _I, _P]),
+    "strassen_select": (_I, [_I64, _I64, _I64, _I, _IP, _IP, _IP]),
+    "strassen_workspace_size": (_I64, [_I64, _I64, _I64, _I, _I, _I]),
+    "strassen_status_string": (ctypes.c_char_p, [_I]),
+    "strassen_plan_table": (_I, [_I, _I, _IP, _IP, _IP, _IP, _IP, _IP]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if the sources changed) and return the CUDA library."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str) -> int:
+    if status != 0:
+        raise StrassenError(status, where)
+    return status
+
+
+# ---------------------------------------------------------------- raw entry points
+
+def strassen_gemm(m, n, k, A, lda, B, ldb, C, ldc, levels, variant, dtype, stream) -> int:
+    """C += A*B (device pointers as ints; stream as a cudaStream_t handle int)."""
+    return lib().strassen_gemm(m, n, k, A, lda, B, ldb, C, ldc, levels, variant, dtype, stream)
+
+
+def classical_gemm(m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
+    return lib().classical_gemm(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def strassen_gemm_batched(count, probs, dtype, stream) -> int:
+    return lib().strassen_gemm_batched(count, probs, dtype, stream)
+
+
+def strassen_select(m, n, k, dtype):
+    lv, var, tile = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = lib().strassen_select(m, n, k, dtype, ctypes.byref(lv), ctypes.byref(var), ctypes.byref(tile))
+    _check(st, "strassen_select")
+    return lv.value, var.value, tile.value
+
+
+def strassen_workspace_size(m, n, k, levels, variant, dtype) -> int:
+    return lib().strassen_workspace_size(m, n, k, levels, variant, dtype)
+
+
+def strassen_status_string(status: int) -> str:
+    return lib().strassen_status_string(status).decode()
+
+
+def strassen_plan_table(levels: int):
+    """The library's coefficient table for ``levels`` as a list of products, each a
+    triple (a_terms, b_terms, c_terms) of (block_row, block_col, sign) tuples."""
+    cap = 49
+    arrs = [(ctypes.c_int * cap)() for _ in range(3)] + [(ctypes.c_int * (4 * cap))() for _ in range(3)]
+    n = lib().strassen_plan_table(levels, cap, *arrs)
+    if n < 0:
+        raise StrassenError(n, "strassen_plan_table")
+    na, nb, nc, ta, tb, tc = arrs
+
+    def dec(v):
+        return ((v // 2) // 16, (v // 2) % 16, -1 if v & 1 else 1)
+
+    out = []
+    for r in range(n):
+        out.append((tuple(dec(ta[r * 4 + t]) for t in range(na[r])),
+                    tuple(dec(tb[r * 4 + t]) for t in range(nb[r])),
+                    tuple(dec(tc[r * 4 + t]) for t in range(nc[r]))))
+    return out

@@ -1,0 +1,298 @@
+// C ABI entry points (include/strassen.h): argument checks, plan selection and the
+// launch sequences of the ABC, AB and Naive variants (Section 4.1).
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+using namespace sgb;
+
+namespace {
+
+int deterministic_requested() {
+  const char* v = std::getenv("STRASSEN_DETERMINISTIC");
+  return v && v[0] && v[0] != '0';
+}
+
+// Shared argument checks of strassen_gemm / classical_gemm.  Returns 1 when the call
+// has nothing to do, 0 when it should proceed, or a negative status.
+int check_args(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+               int64_t ldb, const double* C, int64_t ldc) {
+  if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
+  if (m == 0 || n == 0 || k == 0) return 1;
+  if (!A || !B || !C) return STRASSEN_ERR_NULL;
+  if (lda < k || ldb < n || ldc < n) return STRASSEN_ERR_LD;
+  // C must not overlap A or B (byte ranges of the three operands).
+  const char* a0 = (const char*)A;
+  const char* a1 = (const char*)(A + (m - 1) * lda + k);
+  const char* b0 = (const char*)B;
+  const char* b1 = (const char*)(B + (k - 1) * ldb + n);
+  const char* c0 = (const char*)C;
+  const char* c1 = (const char*)(C + (m - 1) * ldc + n);
+  if ((c0 < a1 && a0 < c1) || (c0 < b1 && b0 < c1)) return STRASSEN_ERR_ARG;
+  return 0;
+}
+
+int clamp_levels(int levels, int64_t m, int64_t n, int64_t k) {
+  int64_t mn = m < n ? m : n;
+  mn = mn < k ? mn : k;
+  while (levels > 0 && ((int64_t)1 << levels) > mn) --levels;
+  return levels;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA; }
+
+// One FP64 product launch over full operands with the given plan.
+Fp64Launch base_launch(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                       const double* B, int64_t ldb, double* C, int64_t ldc, int levels,
+                       const Plan* plan) {
+  Fp64Launch L;
+  std::memset(&L, 0, sizeof(L));
+  L.A = A; L.B = B; L.C = C;
+  L.lda = lda; L.ldb = ldb; L.ldc = ldc;
+  L.a_rows = m; L.a_cols = k;
+  L.b_rows = k; L.b_cols = n;
+  L.c_rows = m; L.c_cols = n;
+  L.hm = block_edge(m, levels); L.hn = block_edge(n, levels); L.hk = block_edge(k, levels);
+  L.plan = plan;
+  L.only_product = -1;
+  L.epi = kEpiAtomicAdd;
+  L.sched = kSchedStreamK;
+  L.tile = 0;
+  return L;
+}
+
+int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                  int64_t ldb, double* C, int64_t ldc, EpilogueKind owner_epi, cudaStream_t s) {
+  Plan pl;
+  make_plan(0, &pl);
+  Fp64Launch L = base_launch(m, n, k, A, lda, B, ldb, C, ldc, 0, &pl);
+  L.epi = owner_epi;
+  choose_fp64_schedule(&L, deterministic_requested());
+  if (owner_epi == kEpiStore && L.sched == kSchedStreamK) {
+    // A plain store cannot take partial sums: clear the destination, then accumulate.
+    if (cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, m, s) != cudaSuccess)
+      return STRASSEN_ERR_CUDA;
+  }
+  return cuda_status(launch_fp64(L, s));
+}
+
+int run_abc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+            int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
+  Plan pl;
+  if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
+  Fp64Launch L = base_launch(m, n, k, A, lda, B, ldb, C, ldc, levels, &pl);
+  L.epi = kEpiAtomicAdd;
+  choose_fp64_schedule(&L, deterministic_requested());
+  return cuda_status(launch_fp64(L, s));
+}
+
+struct Workspace {
+  void* p = nullptr;
+  cudaStream_t s = nullptr;
+  ~Workspace() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+           int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
+  Plan pl;
+  if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
+  const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels);
+  Workspace ws;
+  ws.s = s;
+  if (cudaMallocAsync(&ws.p, sizeof(double) * hm * hn, s) != cudaSuccess) {
+    cudaGetLastError();
+    ws.p = nullptr;
+    return STRASSEN_ERR_ALLOC;
+  }
+  double* M = (double*)ws.p;
+  // The product writes M_r (one target, block (0,0) of M, sign +) ...
+  Plan mp = pl;
+  for (int r = 0; r < mp.nprod; ++r) {
+    mp.nc[r] = 1;
+    mp.tc[r][0] = term_code(0, 0, 0);
+  }
+  for (int r = 0; r < pl.nprod; ++r) {
+    Fp64Launch L = base_launch(m, n, k, A, lda, B, ldb, M, hn, levels, &mp);
+    L.c_rows = hm; L.c_cols = hn;
+    L.only_product = r;
+    L.epi = kEpiStore;
+    choose_fp64_schedule(&L, deterministic_requested());
+    if (L.sched == kSchedStreamK) {
+      if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
+    }
+    cudaError_t e = launch_fp64(L, s);
+    if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    // ... then the separate updates C_q += gamma_q M_r.
+    e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s);
+    if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+  }
+  return STRASSEN_OK;
+}
+
+int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+              int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
+  Plan pl;
+  if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
+  const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
+  Workspace ws;
+  ws.s = s;
+  const int64_t elems = hm * hk + hk * hn + hm * hn;
+  if (cudaMallocAsync(&ws.p, sizeof(double) * elems, s) != cudaSuccess) {
+    cudaGetLastError();
+    ws.p = nullptr;
+    return STRASSEN_ERR_ALLOC;
+  }
+  double* X = (double*)ws.p;
+  double* V = X + hm * hk;
+  double* M = V + hk * hn;
+  for (int r = 0; r < pl.nprod; ++r) {
+    cudaError_t e = launch_block_sum(X, hm, hk, A, lda, m, k, hm, hk, pl.ta[r], pl.na[r], s);
+    if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    e = launch_block_sum(V, hk, hn, B, ldb, k, n, hk, hn, pl.tb[r], pl.nb[r], s);
+    if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    int st = run_classical(hm, hn, hk, X, hk, V, hn, M, hn, kEpiStore, s);
+    if (st != STRASSEN_OK) return st;
+    e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s);
+    if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+  }
+  return STRASSEN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                  int64_t ldb, double* C, int64_t ldc, int levels, strassen_variant variant,
+                  strassen_dtype dtype, strassen_stream_t stream) {
+  try {
+    if (levels < -1 || levels > 2) return STRASSEN_ERR_LEVELS;
+    if ((int)variant < 0 || (int)variant > 3) return STRASSEN_ERR_UNSUPPORTED;
+    if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
+    const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
+    if (chk < 0) return chk;
+    if (chk == 1) return STRASSEN_OK;
+    if (dtype != STRASSEN_F64) return STRASSEN_ERR_UNSUPPORTED;
+    if (levels == -1 || variant == STRASSEN_AUTO) {
+      int sl = 0, tile = 0;
+      strassen_variant sv = STRASSEN_ABC;
+      const int st = strassen_select(m, n, k, dtype, &sl, &sv, &tile);
+      if (st != STRASSEN_OK) return st;
+      if (levels == -1) levels = sl;
+      if (variant == STRASSEN_AUTO) variant = sv;
+    }
+    levels = clamp_levels(levels, m, n, k);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      return STRASSEN_ERR_CUDA;
+    }
+    if (levels == 0) return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, s);
+    switch (variant) {
+      case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
+      case STRASSEN_AB: return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
+      case STRASSEN_NAIVE: return run_naive(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
+      default: return STRASSEN_ERR_UNSUPPORTED;
+    }
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
+}
+
+int classical_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                   int64_t ldb, double* C, int64_t ldc, strassen_stream_t stream) {
+  try {
+    const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
+    if (chk < 0) return chk;
+    if (chk == 1) return STRASSEN_OK;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      return STRASSEN_ERR_CUDA;
+    }
+    return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, (cudaStream_t)stream);
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
+}
+
+int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dtype dtype,
+                          strassen_stream_t stream) {
+  (void)count; (void)probs; (void)dtype; (void)stream;
+  return STRASSEN_ERR_UNSUPPORTED;
+}
+
+int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* levels,
+                    strassen_variant* variant, int* tile_id) {
+  if (!levels || !variant || !tile_id) return STRASSEN_ERR_NULL;
+  if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
+  if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
+  int64_t mn = m < n ? m : n;
+  mn = mn < k ? mn : k;
+  *levels = mn >= 2048 ? 2 : 0;
+  *variant = STRASSEN_ABC;
+  *tile_id = 0;
+  return STRASSEN_OK;
+}
+
+int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant,
+                                strassen_dtype dtype) {
+  if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
+  if (levels < -1 || levels > 2) return STRASSEN_ERR_LEVELS;
+  if ((int)variant < 0 || (int)variant > 3 || (int)dtype < 0 || (int)dtype > 2)
+    return STRASSEN_ERR_UNSUPPORTED;
+  if (m == 0 || n == 0 || k == 0) return 0;
+  if (levels == -1 || variant == STRASSEN_AUTO) {
+    int sl = 0, tile = 0;
+    strassen_variant sv = STRASSEN_ABC;
+    strassen_select(m, n, k, dtype, &sl, &sv, &tile);
+    if (levels == -1) levels = sl;
+    if (variant == STRASSEN_AUTO) variant = sv;
+  }
+  levels = clamp_levels(levels, m, n, k);
+  if (levels == 0 || variant == STRASSEN_ABC) return 0;
+  const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
+  if (variant == STRASSEN_AB) return (int64_t)sizeof(double) * hm * hn;
+  return (int64_t)sizeof(double) * (hm * hk + hk * hn + hm * hn);
+}
+
+const char* strassen_status_string(int status) {
+  switch (status) {
+    case STRASSEN_OK: return "ok";
+    case STRASSEN_ERR_DIM: return "negative dimension";
+    case STRASSEN_ERR_LD: return "leading dimension smaller than the row length";
+    case STRASSEN_ERR_NULL: return "null pointer for a non-empty operand";
+    case STRASSEN_ERR_LEVELS: return "unsupported number of Strassen levels";
+    case STRASSEN_ERR_UNSUPPORTED: return "unsupported dtype or variant";
+    case STRASSEN_ERR_CUDA: return "CUDA error";
+    case STRASSEN_ERR_TIMEOUT: return "device-side wait timed out";
+    case STRASSEN_ERR_ALLOC: return "allocation failed";
+    case STRASSEN_ERR_ARG: return "invalid argument";
+    default: return "unknown status";
+  }
+}
+
+int strassen_plan_table(int levels, int capacity, int* na, int* nb, int* nc, int* a_terms,
+                        int* b_terms, int* c_terms) {
+  Plan pl;
+  if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
+  if (!na || !nb || !nc || !a_terms || !b_terms || !c_terms) return STRASSEN_ERR_NULL;
+  if (capacity < pl.nprod) return STRASSEN_ERR_ARG;
+  auto enc = [](uint8_t c) { return (term_bi(c) * 16 + term_bj(c)) * 2 + term_neg(c); };
+  for (int r = 0; r < pl.nprod; ++r) {
+    na[r] = pl.na[r]; nb[r] = pl.nb[r]; nc[r] = pl.nc[r];
+    for (int t = 0; t < 4; ++t) {
+      a_terms[r * 4 + t] = t < pl.na[r] ? enc(pl.ta[r][t]) : -1;
+      b_terms[r * 4 + t] = t < pl.nb[r] ? enc(pl.tb[r][t]) : -1;
+      c_terms[r * 4 + t] = t < pl.nc[r] ? enc(pl.tc[r][t]) : -1;
+    }
+  }
+  return pl.nprod;
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every symbol the
+header declares, returns the Figure 1 / Figure 2 tables, and rejects bad arguments on
+the host before any CUDA work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1605_01078_gb300 as sg
+from paper_1605_01078_gb300 import _binding
+from oracle import tables
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^\s*(?:STRASSEN_API\s+)?(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(",
+                             src, flags=re.M):
+            names.append(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sg.load_library()
+    names = declared_functions()
+    assert "strassen_gemm" in names and "classical_gemm" in names
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _binding.SIGNATURES, f"binding lacks {name}"
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_plan_table_matches_oracle_tables(levels):
+    assert sg.strassen_plan_table(levels) == tables.table(levels)
+
+
+def test_plan_table_rejects_levels():
+    with pytest.raises(sg.StrassenError):
+        sg.strassen_plan_table(3)
+
+
+P = 0x1000  # a non-null dummy pointer: these calls must fail before touching it
+
+
+@pytest.mark.parametrize("args,status", [
+    ((-1, 4, 4, P, 4, P, 4, P, 4), -1),
+    ((4, 4, 4, 0, 4, P, 4, P, 4), -3),
+    ((4, 4, 4, P, 3, P, 4, 2 * P, 4), -2),
+    ((4, 4, 4, P, 4, P, 3, 2 * P, 4), -2),
+    ((4, 4, 4, P, 4, P, 4, 2 * P, 3), -2),
+    ((4, 4, 4, P, 4, 3 * P, 4, P + 8, 4), -9),   # C overlaps A
+    ((0, 4, 4, 0, 4, 0, 4, 0, 4), 0),             # empty: no-op
+    ((4, 4, 0, 0, 0, 0, 4, 0, 4), 0),
+])
+def test_argument_checks(args, status):
+    st = sg.strassen_gemm(*args, 1, sg.STRASSEN_ABC, sg.STRASSEN_F64, 0)
+    assert st == status, sg.strassen_status_string(st)
+    st2 = sg.classical_gemm(*args, 0)
+    assert st2 == status
+
+
+def test_levels_and_enums_checked():
+    a = (4, 4, 4, P, 4, 2 * P, 4, 3 * P, 4)
+    assert sg.strassen_gemm(*a, 3, 0, 0, 0) == -4
+    assert sg.strassen_gemm(*a, -2, 0, 0, 0) == -4
+    assert sg.strassen_gemm(*a, 1, 7, 0, 0) == -5
+    assert sg.strassen_gemm(*a, 1, 0, 9, 0) == -5
+
+
+def test_workspace_sizes():
+    f = sg.strassen_workspace_size
+    assert f(1024, 1024, 1024, 1, sg.STRASSEN_ABC, 0) == 0
+    assert f(1024, 1024, 1024, 0, sg.STRASSEN_AB, 0) == 0
+    assert f(1024, 1024, 1024, 1, sg.STRASSEN_AB, 0) == 8 * 512 * 512
+    assert f(1000, 998, 7, 2, sg.STRASSEN_NAIVE, 0) == 8 * (250 * 2 + 2 * 250 + 250 * 250)
+    assert f(-1, 4, 4, 1, 0, 0) == -1
+    assert f(4, 4, 4, 5, 0, 0) == -4
+
+
+def test_status_strings():
+    assert sg.strassen_status_string(0) == "ok"
+    assert "dimension" in sg.strassen_status_string(-1)
+    assert sg.strassen_status_string(12345) == "unknown status"
+
+
+def test_select_fixed_rule_without_model():
+    lv, var, tile = sg.strassen_select(8192, 8192, 8192, 0)
+    assert lv in (0, 1, 2) and var in (0, 1, 2) and tile >= 0

@@ -1,0 +1,226 @@
+"""GPU parity of the FP64 path (classical, 1/2-level ABC, AB, Naive) against the CPU
+oracle, through the C ABI.
+
+* Integer-valued inputs: every sum and product is exact in FP64, so the GPU result must
+  equal the oracle bit for bit, for every variant, level and ragged shape.
+* Uniform[-1, 1] inputs, three checks:
+  - normwise: max|C - C_ref| / (||A||_inf * max|B|) <= 1e-13 (classical, one level) or
+    1e-12 (two levels), C_ref from the oracle's classical definition (or its
+    Dot2-compensated entries at full benchmark size).  ||A||_inf * max|B| bounds
+    max|A B|, so this is the max-norm error relative to the size of the product;
+  - classical: every entry within the rounding bound gamma_{k+1} (|C0| + |A||B|) of the
+    exact result, which holds for any summation order;
+  - Strassen: no less accurate than the oracle's textbook recursive Strassen with the
+    same number of levels: max|C - C_exact| <= 2 max|C_textbook - C_exact| + 2u max|C_exact|.
+"""
+import functools
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import paper_1605_01078_gb300 as sg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ["ABC", "AB", "NAIVE"]
+TOL = {0: 1e-13, 1: 1e-13, 2: 1e-12}
+U = 2.0 ** -53
+
+
+def normwise_err(C, C_ref, A, B):
+    """max|C - C_ref| / (||A||_inf max|B|), ||A||_inf the largest absolute row sum."""
+    den = float(np.max(np.sum(np.abs(A), axis=1))) * float(np.max(np.abs(B)))
+    return float(np.max(np.abs(C - C_ref))) / den
+
+
+def gamma(n):
+    return n * U / (1 - n * U)
+
+
+def exact_full(A, B, C):
+    m, n = C.shape
+    rows, cols = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    return oracle.gemm_sampled(np.ascontiguousarray(A), np.ascontiguousarray(B), np.ascontiguousarray(C),
+                               rows.ravel(), cols.ravel()).reshape(m, n)
+
+
+@functools.lru_cache(maxsize=4)
+def float_case(m, n, k, sa, sb, sc, zero_c):
+    A, B = W.uniform(m, k, sa), W.uniform(k, n, sb)
+    C = np.zeros((m, n)) if zero_c else W.uniform(m, n, sc)
+    ref = ref_gemm(A, B, C)
+    exact = exact_full(A, B, C)
+    textbook = {}
+    for L in (1, 2):
+        t = np.array(C, copy=True)
+        oracle.strassen(A, B, t, L)
+        textbook[L] = float(np.max(np.abs(t - exact)))
+    return A, B, C, ref, exact, textbook
+
+
+def check_float(got, levels, case):
+    A, B, C, ref, exact, textbook = case
+    assert normwise_err(got, ref, A, B) <= TOL[levels]
+    if levels == 0:
+        bound = gamma(A.shape[1] + 1) * (np.abs(C) + np.abs(A) @ np.abs(B))
+        assert np.all(np.abs(got - exact) <= bound)
+    else:
+        err = float(np.max(np.abs(got - exact)))
+        assert err <= 2 * textbook[levels] + 2 * U * float(np.max(np.abs(exact))), (err, textbook[levels])
+
+
+def dev(x: np.ndarray, ld: int | None = None):
+    """Copy a row-major numpy matrix to the GPU; with ld > cols the device buffer has
+    NaN padding columns (a kernel reading them would poison the result)."""
+    rows, cols = x.shape
+    if ld is None or ld == cols:
+        return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    buf = torch.full((rows, ld), float("nan"), dtype=torch.float64, device="cuda")
+    buf[:, :cols] = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return buf[:, :cols]
+
+
+def run(A, B, C, levels, variant):
+    if variant == "classical":
+        sg.classical(A, B, C)
+    else:
+        sg.gemm(A, B, C, levels=levels, variant=variant)
+    torch.cuda.synchronize()
+
+
+def ref_gemm(A, B, C):
+    out = np.array(C, copy=True)
+    oracle.gemm(np.ascontiguousarray(A), np.ascontiguousarray(B), out)
+    return out
+
+
+SHAPES_INT = [(16, 16, 16), (1, 1, 1), (2, 3, 5), (13, 7, 11), (130, 257, 129), (300, 200, 513), (64, 520, 96)]
+
+
+@pytest.mark.parametrize("m,n,k", SHAPES_INT)
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_integer_bit_exact(m, n, k, levels, variant):
+    A, B, C = W.integer(m, k, 1), W.integer(k, n, 2), W.integer(m, n, 3)
+    ref = ref_gemm(A, B, C)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    run(dA, dB, dC, levels, variant)
+    got = dC.cpu().numpy()
+    assert np.array_equal(got, ref), f"max diff {np.max(np.abs(got - ref))}"
+
+
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (130, 257, 129)])
+def test_classical_integer_bit_exact(m, n, k):
+    A, B, C = W.integer(m, k, 4), W.integer(k, n, 5), W.integer(m, n, 6)
+    dC = dev(C)
+    run(dev(A), dev(B), dC, 0, "classical")
+    assert np.array_equal(dC.cpu().numpy(), ref_gemm(A, B, C))
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_float_ragged_tolerance(levels, variant):
+    case = float_case(255, 333, 517, 7, 8, 9, False)
+    dC = dev(case[2])
+    run(dev(case[0]), dev(case[1]), dC, levels, variant)
+    check_float(dC.cpu().numpy(), levels, case)
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_config_1024(levels, variant):
+    """m = n = k = 1024, lda = ldb = ldc = 1024, uniform[-1, 1] from a seed, C = 0."""
+    case = float_case(1024, 1024, 1024, 0, 1, 0, True)
+    dC = dev(case[2])
+    run(dev(case[0]), dev(case[1]), dC, levels, variant)
+    check_float(dC.cpu().numpy(), levels, case)
+
+
+def test_leading_dimensions_and_padding_untouched():
+    m, n, k = 97, 131, 77
+    A, B, C = W.integer(m, k, 11), W.integer(k, n, 12), W.integer(m, n, 13)
+    ref = ref_gemm(A, B, C)
+    for levels in (0, 1, 2):
+        for variant in VARIANTS:
+            dA, dB = dev(A, ld=k + 3), dev(B, ld=n + 5)
+            cbuf = torch.full((m, n + 7), 777.0, dtype=torch.float64, device="cuda")
+            cbuf[:, :n] = torch.from_numpy(C).cuda()
+            dC = cbuf[:, :n]
+            run(dA, dB, dC, levels, variant)
+            got = cbuf.cpu().numpy()
+            assert np.array_equal(got[:, :n], ref), (levels, variant)
+            assert np.all(got[:, n:] == 777.0), (levels, variant)
+
+
+def test_odd_leading_dimension_float():
+    m, n, k = 200, 150, 301
+    A, B, C = W.uniform(m, k, 14), W.uniform(k, n, 15), W.uniform(m, n, 16)
+    ref = ref_gemm(A, B, C)
+    for levels in (1, 2):
+        dC = dev(C, ld=n + 1)
+        run(dev(A, ld=k + 1), dev(B, ld=n + 3), dC, levels, "ABC")
+        assert normwise_err(dC.cpu().numpy(), ref, A, B) <= TOL[levels]
+
+
+def test_empty_and_degenerate_sizes():
+    z = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    assert sg.strassen_gemm(0, 4, 4, 0, 4, 0, 4, 0, 4, 1, 0, 0, 0) == 0
+    assert sg.strassen_gemm(4, 4, 0, 0, 4, 0, 4, z.data_ptr(), 4, 1, 0, 0, 0) == 0
+    assert torch.all(z == 0)
+    # levels clamp: 2 levels on a 3 x 3 x 3 product still computes it exactly
+    A, B = W.integer(3, 3, 1), W.integer(3, 3, 2)
+    dC = dev(np.zeros((3, 3)))
+    sg.gemm(dev(A), dev(B), dC, levels=2, variant="ABC")
+    torch.cuda.synchronize()
+    assert np.array_equal(dC.cpu().numpy(), A @ B)
+
+
+def test_deterministic_mode_is_bitwise_repeatable(monkeypatch):
+    monkeypatch.setenv("STRASSEN_DETERMINISTIC", "1")
+    n = 700
+    A, B = dev(W.uniform(n, n, 1)), dev(W.uniform(n, n, 2))
+    outs = []
+    for _ in range(2):
+        C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        sg.gemm(A, B, C, levels=2, variant="ABC")
+        torch.cuda.synchronize()
+        outs.append(C.cpu())
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_runs_on_a_side_stream():
+    s = torch.cuda.Stream()
+    A, B = W.integer(300, 200, 1), W.integer(200, 100, 2)
+    dA, dB = dev(A), dev(B)
+    dC = torch.zeros((300, 100), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        sg.gemm(dA, dB, dC, levels=1, variant="AB", stream=s)
+    s.synchronize()
+    assert np.array_equal(dC.cpu().numpy(), A @ B)
+
+
+@pytest.mark.parametrize("levels,variant", [(2, "ABC"), (1, "ABC"), (0, "classical")])
+def test_full_size_sampled_against_dot2(levels, variant):
+    """The benchmark's size (m = n = k = 8192, accumulate mode), checked on sampled
+    entries the oracle computes one by one with Dot2."""
+    n = 8192
+    A, B, C = W.uniform(n, n, 100), W.uniform(n, n, 101), W.uniform(n, n, 102)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    run(dA, dB, dC, levels, variant)
+    rows, cols = W.sample_indices(n, n, 512, 7)
+    ref = oracle.gemm_sampled(A, B, C, rows, cols)
+    got = dC.cpu().numpy()[rows, cols]
+    den = float(np.max(np.sum(np.abs(A), axis=1))) * float(np.max(np.abs(B)))
+    assert float(np.max(np.abs(got - ref))) / den <= TOL[levels]
+    if levels == 0:
+        absdot = np.einsum("ij,ji->i", np.abs(A[rows, :]), np.abs(B[:, cols]))
+        assert np.all(np.abs(got - ref) <= gamma(n + 1) * (np.abs(C[rows, cols]) + absdot))
+    else:
+        # elementwise error stays within the strict max-norm tolerance scaled by k
+        assert float(np.max(np.abs(got - ref))) <= TOL[levels] * n
