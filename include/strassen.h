@@ -87,6 +87,8 @@ typedef enum {
 #define STRASSEN_ERR_TIMEOUT (-7)     /* a device-side wait gave up (batched work queue) */
 #define STRASSEN_ERR_ALLOC (-8)       /* a temporary could not be allocated */
 #define STRASSEN_ERR_ARG (-9)         /* any other invalid argument (count, pointer array, ...) */
+#define STRASSEN_ERR_SCRATCH_LIMIT (-10) /* the product needs more than the fixed scratch array of
+                                            strassen_gemm_ab_noalloc holds */
 
 /*
  * strassen_gemm -- C += A*B with `levels` levels of Strassen in `variant`.
@@ -186,6 +188,39 @@ STRASSEN_API int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype
  */
 STRASSEN_API int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels,
                                 strassen_variant variant, strassen_dtype dtype);
+
+/*
+ * strassen_gemm_ab_noalloc -- the AB variant (levels 1 or 2) that allocates nothing.
+ * The paper has no counterpart: it is an interface for callers that cannot allocate
+ * device memory while they run -- a process whose device memory is already claimed by
+ * its own pooling allocator, a latency-bound loop where an allocation or a free may
+ * synchronise the device, or code that must have no out-of-memory failure path.
+ *
+ * Computes C += A*B exactly as strassen_gemm(..., levels, STRASSEN_AB, STRASSEN_F64,
+ * stream) does (same arguments, layout, ownership and checks), but the temporary
+ * M_r of (ceil(m/2^L) x ceil(n/2^L)) doubles lives in one fixed array of 4 Mi doubles
+ * (32 MiB) compiled into the library, so the call makes no cudaMalloc, cudaFree or
+ * other allocating call.  Every GPU that loads the library holds that array until the
+ * process exits.
+ *
+ *   Limit:   ceil(m/2^L) * ceil(n/2^L) <= 4194304 (e.g. m = n = 4096 at one level,
+ *            8192 at two); larger products return STRASSEN_ERR_SCRATCH_LIMIT and touch
+ *            nothing.  levels outside {1, 2} return STRASSEN_ERR_LEVELS (levels are
+ *            clamped as in strassen_gemm; a clamp to 0 runs classical_gemm).
+ *   Set-up:  the first call on each device looks up the array's device address with
+ *            cudaGetSymbolAddress while that device is current; make that first call
+ *            before any stream capture.
+ *   Sharing: all calls in the process share the one array and it keeps the last
+ *            call's contents (the kernels overwrite or clear what they read).  Calls
+ *            whose work overlaps on the GPU (different streams, or different host
+ *            threads without ordering) race on the array and give wrong results:
+ *            order them on one stream or synchronise between them.
+ */
+STRASSEN_API int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k,
+                                          const double* A, int64_t lda,
+                                          const double* B, int64_t ldb,
+                                          double* C, int64_t ldc,
+                                          int levels, strassen_stream_t stream);
 
 /* strassen_status_string -- a static, NUL-terminated description of a status code. */
 STRASSEN_API const char* strassen_status_string(int status);

@@ -16,7 +16,8 @@ from __future__ import annotations
 from . import _binding
 from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  # noqa: F401
                        STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_NAIVE, StrassenError,
-                       classical_gemm, strassen_gemm, strassen_gemm_batched, strassen_plan_table,
+                       classical_gemm, strassen_gemm, strassen_gemm_ab_noalloc, strassen_gemm_batched,
+                       strassen_plan_table,
                        strassen_problem, strassen_select, strassen_status_string,
                        strassen_workspace_size)
 

@@ -22,6 +22,7 @@ STATUS = {
     0: "STRASSEN_OK", -1: "STRASSEN_ERR_DIM", -2: "STRASSEN_ERR_LD", -3: "STRASSEN_ERR_NULL",
     -4: "STRASSEN_ERR_LEVELS", -5: "STRASSEN_ERR_UNSUPPORTED", -6: "STRASSEN_ERR_CUDA",
     -7: "STRASSEN_ERR_TIMEOUT", -8: "STRASSEN_ERR_ALLOC", -9: "STRASSEN_ERR_ARG",
+    -10: "STRASSEN_ERR_SCRATCH_LIMIT",
 }
 
 
@@ -50,6 +51,7 @@ SIGNATURES = {
     "strassen_workspace_size": (_I64, [_I64, _I64, _I64, _I, _I, _I]),
     "strassen_status_string": (ctypes.c_char_p, [_I]),
     "strassen_plan_table": (_I, [_I, _I, _IP, _IP, _IP, _IP, _IP, _IP]),
+    "strassen_gemm_ab_noalloc": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _P]),
 }
 
 
@@ -85,6 +87,12 @@ def strassen_gemm(m, n, k, A, lda, B, ldb, C, ldc, levels, variant, dtype, strea
 
 def classical_gemm(m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
     return lib().classical_gemm(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def strassen_gemm_ab_noalloc(m, n, k, A, lda, B, ldb, C, ldc, levels, stream) -> int:
+    """AB Strassen with its temporary in the library's fixed device array: no device
+    allocation in the call (for callers that cannot allocate while they run)."""
+    return lib().strassen_gemm_ab_noalloc(m, n, k, A, lda, B, ldb, C, ldc, levels, stream)
 
 
 def strassen_gemm_batched(count, probs, dtype, stream) -> int:

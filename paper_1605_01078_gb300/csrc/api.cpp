@@ -273,6 +273,7 @@ const char* strassen_status_string(int status) {
     case STRASSEN_ERR_TIMEOUT: return "device-side wait timed out";
     case STRASSEN_ERR_ALLOC: return "allocation failed";
     case STRASSEN_ERR_ARG: return "invalid argument";
+    case STRASSEN_ERR_SCRATCH_LIMIT: return "product too large for the fixed scratch array of the no-allocation entry point";
     default: return "unknown status";
   }
 }
