@@ -85,29 +85,17 @@ extern "C" int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k, const d
   }
   Plan pl;
   if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
-  Plan mp = pl;  // each product writes M_r into block (0,0) of M with sign +
-  for (int r = 0; r < mp.nprod; ++r) {
-    mp.nc[r] = 1;
-    mp.tc[r][0] = term_code(0, 0, 0);
-  }
   for (int r = 0; r < pl.nprod; ++r) {
-    Fp64Launch L;
-    L.A = A; L.B = B; L.C = M;
-    L.lda = lda; L.ldb = ldb; L.ldc = hn;
-    L.a_rows = m; L.a_cols = k; L.b_rows = k; L.b_cols = n;
+    // Each product writes M_r into block (0,0) of M with sign +.
+    Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, M, hn, levels);
     L.c_rows = hm; L.c_cols = hn;
-    L.hm = hm; L.hn = hn; L.hk = block_edge(k, levels);
-    L.plan = &mp;
-    L.only_product = r;
+    L.prod_begin = r; L.nprod = 1;
+    L.m_target = 1;
     L.epi = kEpiStore;
-    L.sched = kSchedOwner;
-    L.tile = 0;
     choose_fp64_schedule(&L, 0);
-    // The array keeps the previous call's contents: when partial sums are accumulated
-    // (split schedule) M must start at zero.
-    if (L.sched == kSchedStreamK &&
-        cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess)
-      return STRASSEN_ERR_CUDA;
+    // The array keeps the previous call's contents and the kernel accumulates into
+    // it: clear M first.
+    if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
     if (launch_fp64(L, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
     if (launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s) != cudaSuccess)
       return STRASSEN_ERR_CUDA;

@@ -45,35 +45,13 @@ int clamp_levels(int levels, int64_t m, int64_t n, int64_t k) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA; }
 
-// One FP64 product launch over full operands with the given plan.
-Fp64Launch base_launch(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
-                       const double* B, int64_t ldb, double* C, int64_t ldc, int levels,
-                       const Plan* plan) {
-  Fp64Launch L;
-  std::memset(&L, 0, sizeof(L));
-  L.A = A; L.B = B; L.C = C;
-  L.lda = lda; L.ldb = ldb; L.ldc = ldc;
-  L.a_rows = m; L.a_cols = k;
-  L.b_rows = k; L.b_cols = n;
-  L.c_rows = m; L.c_cols = n;
-  L.hm = block_edge(m, levels); L.hn = block_edge(n, levels); L.hk = block_edge(k, levels);
-  L.plan = plan;
-  L.only_product = -1;
-  L.epi = kEpiAtomicAdd;
-  L.sched = kSchedStreamK;
-  L.tile = 0;
-  return L;
-}
-
 int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                   int64_t ldb, double* C, int64_t ldc, EpilogueKind owner_epi, cudaStream_t s) {
-  Plan pl;
-  make_plan(0, &pl);
-  Fp64Launch L = base_launch(m, n, k, A, lda, B, ldb, C, ldc, 0, &pl);
+  Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, C, ldc, 0);
   L.epi = owner_epi;
   choose_fp64_schedule(&L, deterministic_requested());
-  if (owner_epi == kEpiStore && L.sched == kSchedStreamK) {
-    // A plain store cannot take partial sums: clear the destination, then accumulate.
+  if (owner_epi == kEpiStore) {
+    // The kernel accumulates into its target: a store is a clear followed by the adds.
     if (cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, m, s) != cudaSuccess)
       return STRASSEN_ERR_CUDA;
   }
@@ -82,9 +60,7 @@ int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
 
 int run_abc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
             int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
-  Plan pl;
-  if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
-  Fp64Launch L = base_launch(m, n, k, A, lda, B, ldb, C, ldc, levels, &pl);
+  Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, C, ldc, levels);
   L.epi = kEpiAtomicAdd;
   choose_fp64_schedule(&L, deterministic_requested());
   return cuda_status(launch_fp64(L, s));
@@ -111,21 +87,16 @@ int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
     return STRASSEN_ERR_ALLOC;
   }
   double* M = (double*)ws.p;
-  // The product writes M_r (one target, block (0,0) of M, sign +) ...
-  Plan mp = pl;
-  for (int r = 0; r < mp.nprod; ++r) {
-    mp.nc[r] = 1;
-    mp.tc[r][0] = term_code(0, 0, 0);
-  }
   for (int r = 0; r < pl.nprod; ++r) {
-    Fp64Launch L = base_launch(m, n, k, A, lda, B, ldb, M, hn, levels, &mp);
+    // The product writes M_r (one target: block (0,0) of M, sign +) ...
+    Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, M, hn, levels);
     L.c_rows = hm; L.c_cols = hn;
-    L.only_product = r;
+    L.prod_begin = r; L.nprod = 1;
+    L.m_target = 1;
     L.epi = kEpiStore;
     choose_fp64_schedule(&L, deterministic_requested());
-    if (L.sched == kSchedStreamK) {
-      if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
-    }
+    // The kernel accumulates into M: clear it first.
+    if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
     cudaError_t e = launch_fp64(L, s);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
     // ... then the separate updates C_q += gamma_q M_r.

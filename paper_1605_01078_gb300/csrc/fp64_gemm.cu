@@ -1,264 +1,433 @@
 // FP64 product kernel: the general operation of Eq. 4 on GB300.
 //
-// One persistent launch runs every product M_r of a plan (Figure 1 / Figure 2 table)
-// over a set of work units (product r, output tile of the block, k-steps).  Per k-step
-// a thread block
-//   1. stages the 1..4 source tiles of A (blocks X_s) and of B (blocks V_t) into a
-//      shared-memory ring with cp.async (8-byte copies, zero-filled outside the block
-//      and outside the matrix: the virtual padding of Section 3.3),
-//   2. forms the operand sums sum_s delta_s X_s and sum_t eps_t V_t from that ring into
-//      a double-buffered "summed" tile (the packing-time sums of Section 3.4: no
-//      temporary in global memory),
-//   3. accumulates M_tile += A_sum * B_sum with FP64 fused multiply-adds in registers
-//      (an 8x8 or 4x4 register tile per thread),
-// and after the last k-step of a unit adds gamma_q * M_tile into every C block q the
-// product updates (the fused scatter of the micro-kernel, Section 3.4).
+// One persistent launch runs every product M_r of one or more problems (Figure 1 /
+// Figure 2 tables) over work units (problem, product r, 128x128 output tile of the
+// block, k-steps of 8).  Each thread block is warp-specialised:
+//
+//   producer warps (4)  stage the 1..4 source tiles of A (blocks X_s) and of B
+//       (blocks V_t) of a k-step into a shared-memory ring -- with TMA box loads
+//       (cp.async.bulk.tensor, completion on an mbarrier) when the operands are
+//       16-byte aligned, else with zero-filling 8-byte cp.async -- and form the
+//       operand sums sum_s delta_s X_s and sum_t eps_t V_t into a ring of "summed"
+//       tiles: the packing-time sums of Section 3.4, with no temporary in global
+//       memory.  Columns past the block edge h_k read as zero (the zero padding of
+//       Section 3.3); TMA zero-fills past the matrix edge.
+//   consumer warps (8)  accumulate M_tile += A_sum * B_sum with FP64 fused
+//       multiply-adds on an 8x8 register tile per thread and, after the last k-step of
+//       a unit, add gamma_q * M_tile into every C block q the product updates -- the
+//       fused scatter of the micro-kernel (Section 3.4).
+//
+// C updates are device atomics (red.global.add.f64) for every schedule; a store into a
+// temporary is a clear followed by adds.  The two groups hand tiles over through
+// mbarriers; every wait is bounded (about one
+// second of clock cycles), after which the kernel records STRASSEN_ERR_TIMEOUT in a
+// device status word and returns instead of hanging.
 //
 // GB300 design notes.  FP64 runs at about 2 FMA lanes per clock per SM (measured
-// 1.20 TFLOP/s for the whole GPU, DMMA 1.06), so every kernel here is bound by the
-// FP64 pipe by more than two orders of magnitude over HBM: the design minimises FP64
-// instructions (operand sums are formed once per staged tile, C updates once per unit,
-// negations are sign-bit flips) and balances work across the 152 SMs exactly
-// (stream-K ranges of the (unit, k-step) space), instead of chasing memory traffic.
-// Atomic C updates (red.global.add.f64) execute in the L2, not in the SM's FP64 pipe.
+// 1.20 TFLOP/s for the whole GPU; DMMA is slower at 1.06), so this kernel is bound by
+// the FP64 pipe by two orders of magnitude over HBM.  The design therefore keeps the
+// FP64 pipe fed with nothing but the product's FMAs in the consumer warps (staging,
+// address arithmetic, operand sums and barrier traffic live in the producer warps),
+// forms each operand sum once per staged tile, uses sign-bit flips for negation, and
+// balances work across the 152 SMs exactly (stream-K ranges of the (unit, k-step)
+// space).  Atomic C updates (red.global.add.f64) execute in the L2, off the SM's FP64
+// pipe.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
 namespace sgb {
 namespace {
 
-struct KParams {
+__constant__ PlanTables c_plans = kPlanTables;
+__device__ int g_fp64_status;  // STRASSEN_ERR_TIMEOUT once a bounded wait gave up
+
+constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
+constexpr int kConsumers = 256;  // 8 warps: 16 x 16 threads, 8 x 8 outputs each
+constexpr int kProducers = 128;  // 4 warps: staging and operand sums
+constexpr int kThreads = kConsumers + kProducers;
+constexpr int NR = 2;  // ring of raw source tiles
+constexpr int NS = 4;  // ring of summed tiles
+constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
+// Register split (setmaxnreg): the block is launched with kLaunchRegs per thread;
+// the producer warpgroup gives registers back and the two consumer warpgroups take
+// them.  The shares add up exactly to the launch total, so the increase never waits
+// on registers that do not exist.
+constexpr int kLaunchRegs = 168, kProducerRegs = 72, kConsumerRegs = 216;
+static_assert(kProducers * kProducerRegs + kConsumers * kConsumerRegs == kThreads * kLaunchRegs,
+              "register split must add up to the launch allocation");
+
+struct alignas(128) ProbDesc {
+  CUtensorMap tmA, tmB;
   const double* A;
   const double* B;
   double* C;
   int64_t lda, ldb, ldc;
   int64_t a_rows, a_cols, b_rows, b_cols, c_rows, c_cols;
   int64_t hm, hn, hk;
-  int64_t total;  // stream-K: nprod * tiles * ksteps iterations; owner: tile positions
-  int nprod;
-  int tiles_m, tiles_n, ksteps;
-  int epi, sched;
-  uint8_t na[kMaxProducts], nb[kMaxProducts], nc[kMaxProducts];
-  uint8_t ta[kMaxProducts][kMaxTerms], tb[kMaxProducts][kMaxTerms], tc[kMaxProducts][kMaxTerms];
+  int64_t iter_begin;  // first iteration of this problem in the stream-K space
+  int32_t plan_row;    // table row of the first product of this problem
+  int32_t nprod;
+  int32_t m_target;
+  int32_t epi;
+  int32_t tiles_m, tiles_n, ksteps;
+  int32_t use_tma;
 };
 
+struct KArgs {
+  ProbDesc single;         // the problem when not batched
+  const ProbDesc* descs;   // device array when batched
+  int nprob;
+  int sched;
+  int64_t total;           // stream-K: iterations of all problems; owner: tile positions
+};
+
+template <int MAXT>
+struct Smem {
+  static constexpr int kRawA = MAXT * BM * BK;  // doubles per ring slot
+  static constexpr int kRawB = MAXT * BK * BN;
+  static constexpr size_t kBytes =
+      sizeof(double) * (size_t)(NR * (kRawA + kRawB) + NS * BK * (BM + BN) + (kConsumers / 32) * 2 * BN) +
+      sizeof(uint64_t) * (2 * NR + 2 * NS);
+};
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitLimitCycles) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ double flip_sign(double x, int neg) {
   return __longlong_as_double(__double_as_longlong(x) ^ ((long long)neg << 63));
 }
+__device__ __forceinline__ void record_timeout() { atomicExch(&g_fp64_status, STRASSEN_ERR_TIMEOUT); }
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// ---------------------------------------------------------------- work cursor
 
-struct Step {
-  int r, tm, tn, ks;
-  bool last;  // last k-step of this unit inside this block's range: run the epilogue
+// Walks this block's sequence of (problem, product, tile, k-step) without divisions
+// after the start.  Producers and consumers each keep one.
+struct Cursor {
+  int p, r, t, ks;
+  int64_t left;  // steps left, including the current one
 };
 
-// Local step j of this block -> (product, tile, k-step).
-__device__ __forceinline__ Step decode(const KParams& p, int64_t beg, int64_t end, int64_t j) {
-  Step s;
-  const int tiles = p.tiles_m * p.tiles_n;
-  if (p.sched == kSchedStreamK) {
-    const int64_t g = beg + j;
-    const int64_t u = g / p.ksteps;
-    s.ks = (int)(g - u * p.ksteps);
-    s.r = (int)(u / tiles);
-    const int t = (int)(u - (int64_t)s.r * tiles);
-    s.tm = t / p.tiles_n;
-    s.tn = t - s.tm * p.tiles_n;
-    s.last = (s.ks == p.ksteps - 1) || (g == end - 1);
+template <bool BATCHED>
+__device__ __forceinline__ const ProbDesc& desc_of(const KArgs& a, int p) {
+  if constexpr (BATCHED) return a.descs[p];
+  else return a.single;
+}
+
+template <bool BATCHED>
+__device__ Cursor cursor_begin(const KArgs& a, int64_t* count_out) {
+  Cursor c;
+  c.p = 0; c.r = 0; c.t = 0; c.ks = 0; c.left = 0;
+  if (a.sched == kSchedStreamK) {
+    const int64_t beg = (a.total * (int64_t)blockIdx.x) / gridDim.x;
+    const int64_t end = (a.total * (int64_t)(blockIdx.x + 1)) / gridDim.x;
+    c.left = end - beg;
+    if (c.left > 0) {
+      int p = 0;
+      if constexpr (BATCHED) {  // last problem whose first iteration is <= beg
+        int lo = 0, hi = a.nprob - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) / 2;
+          if (a.descs[mid].iter_begin <= beg) lo = mid; else hi = mid - 1;
+        }
+        p = lo;
+      }
+      const ProbDesc& d = desc_of<BATCHED>(a, p);
+      const int64_t local = beg - d.iter_begin;
+      const int64_t u = local / d.ksteps;
+      const int tiles = d.tiles_m * d.tiles_n;
+      c.p = p;
+      c.ks = (int)(local - u * d.ksteps);
+      c.r = (int)(u / tiles);
+      c.t = (int)(u - (int64_t)c.r * tiles);
+    }
   } else {
-    const int64_t per_tile = (int64_t)p.nprod * p.ksteps;
-    const int64_t q = j / per_tile;
-    const int64_t rem = j - q * per_tile;
-    s.r = (int)(rem / p.ksteps);
-    s.ks = (int)(rem - (int64_t)s.r * p.ksteps);
-    const int t = (int)(blockIdx.x + q * gridDim.x);
-    s.tm = t / p.tiles_n;
-    s.tn = t - s.tm * p.tiles_n;
-    s.last = (s.ks == p.ksteps - 1);
+    const ProbDesc& d = desc_of<BATCHED>(a, 0);
+    const int64_t owned = (a.total > blockIdx.x) ? (a.total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    c.left = owned * d.nprod * d.ksteps;
+    c.t = blockIdx.x;
   }
-  return s;
+  *count_out = c.left;
+  return c;
 }
 
-template <int BM, int BN, int BK, int TM, int TN, int MAXT, int NS>
-struct Cfg {
-  static constexpr int kThreads = (BM / TM) * (BN / TN);
-  static constexpr int kRawA = MAXT * BK * BM;  // doubles per stage
-  static constexpr int kRawB = MAXT * BK * BN;
-  static constexpr size_t kSmem = sizeof(double) * (size_t)(NS * (kRawA + kRawB) + 2 * BK * (BM + BN));
-};
+template <bool BATCHED>
+__device__ __forceinline__ bool cursor_last(const KArgs& a, const Cursor& c) {
+  const ProbDesc& d = desc_of<BATCHED>(a, c.p);
+  return c.ks == d.ksteps - 1 || (a.sched == kSchedStreamK && c.left == 1);
+}
 
-template <int BM, int BN, int BK, int TM, int TN, int MAXT, int NS>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-fp64_strassen_kernel(const __grid_constant__ KParams p) {
-  using C_ = Cfg<BM, BN, BK, TM, TN, MAXT, NS>;
-  constexpr int NT = C_::kThreads;
-  static_assert((BM * BK) % NT == 0 && (BN * BK) % NT == 0, "tile/thread mismatch");
-  extern __shared__ __align__(16) double smem[];
-  double* rawA = smem;                         // [NS][MAXT][BK][BM]
-  double* rawB = rawA + NS * C_::kRawA;        // [NS][MAXT][BK][BN]
-  double* sumA = rawB + NS * C_::kRawB;        // [2][BK][BM]
-  double* sumB = sumA + 2 * BK * BM;           // [2][BK][BN]
+template <bool BATCHED>
+__device__ __forceinline__ void cursor_next(const KArgs& a, Cursor& c) {
+  const ProbDesc& d = desc_of<BATCHED>(a, c.p);
+  --c.left;
+  if (++c.ks < d.ksteps) return;
+  c.ks = 0;
+  if (a.sched == kSchedStreamK) {
+    if (++c.t < d.tiles_m * d.tiles_n) return;
+    c.t = 0;
+    if (++c.r < d.nprod) return;
+    c.r = 0;
+    ++c.p;
+  } else {
+    if (++c.r < d.nprod) return;
+    c.r = 0;
+    c.t += gridDim.x;
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+
+template <int MAXT, bool BATCHED>
+__global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid_constant__ KArgs a) {
+  using S = Smem<MAXT>;
+  extern __shared__ __align__(128) double smem[];
+  double* rawA = smem;                    // [NR][MAXT][BM][BK]   (TMA box layout: row, k)
+  double* rawB = rawA + NR * S::kRawA;    // [NR][MAXT][BK][BN]
+  double* sumA = rawB + NR * S::kRawB;    // [NS][BK][BM]         (k-major for the consumers)
+  double* sumB = sumA + NS * BK * BM;     // [NS][BK][BN]
+  double* epi_stage = sumB + NS * BK * BN;  // [consumer warp][2][BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_stage + (kConsumers / 32) * 2 * BN);
+  uint64_t* raw_full = bars;              // count kProducers (+ TMA bytes)
+  uint64_t* raw_empty = bars + NR;        // count kProducers
+  uint64_t* sum_full = bars + 2 * NR;     // count kProducers
+  uint64_t* sum_empty = bars + 2 * NR + NS;  // count kConsumers
 
   const int tid = threadIdx.x;
-  // This block's share of the work.
-  int64_t beg = 0, end = 0, count = 0;
-  if (p.sched == kSchedStreamK) {
-    beg = (p.total * (int64_t)blockIdx.x) / gridDim.x;
-    end = (p.total * (int64_t)(blockIdx.x + 1)) / gridDim.x;
-    count = end - beg;
-  } else {
-    const int64_t owned = (p.total > blockIdx.x) ? (p.total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    count = owned * p.nprod * p.ksteps;
+  if (tid == 0) {
+    for (int i = 0; i < NR; ++i) { mbar_init(&raw_full[i], kProducers); mbar_init(&raw_empty[i], kProducers); }
+    for (int i = 0; i < NS; ++i) { mbar_init(&sum_full[i], kProducers); mbar_init(&sum_empty[i], kConsumers); }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
+  if constexpr (BATCHED) {
+    // Descriptors were written by a copy before the launch: make the tensor maps
+    // visible to the TMA unit.
+    if (tid == kConsumers) {
+      for (int p = 0; p < a.nprob; ++p) {
+        if (!a.descs[p].use_tma) continue;
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(&a.descs[p].tmA) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(&a.descs[p].tmB) : "memory");
+      }
+    }
+  }
+  __syncthreads();
+
+  int64_t count = 0;
+  Cursor cur = cursor_begin<BATCHED>(a, &count);
   if (count <= 0) return;
 
-  // Issue the cp.async copies of the source tiles of step j into ring slot j % NS.
-  auto load_step = [&](int64_t j) {
-    const Step s = decode(p, beg, end, j);
-    const int slot = (int)(j % NS);
-    double* ra = rawA + slot * C_::kRawA;
-    double* rb = rawB + slot * C_::kRawB;
-    const int na = min((int)p.na[s.r], MAXT), nb = min((int)p.nb[s.r], MAXT);
-    for (int t = 0; t < na; ++t) {
-      const uint8_t code = p.ta[s.r][t];
-      const int64_t r0 = (int64_t)term_bi(code) * p.hm, c0 = (int64_t)term_bj(code) * p.hk;
-#pragma unroll
-      for (int q = 0; q < (BM * BK) / NT; ++q) {
-        const int e = tid + q * NT;
-        const int i = e / BK, kk = e - (e / BK) * BK;
-        const int64_t li = (int64_t)s.tm * BM + i, lk = (int64_t)s.ks * BK + kk;
-        const int64_t gr = r0 + li, gc = c0 + lk;
-        const bool ok = li < p.hm && lk < p.hk && gr < p.a_rows && gc < p.a_cols;
-        const double* src = ok ? p.A + gr * p.lda + gc : p.A;
-        cp_async8(ra + (t * BK + kk) * BM + i, src, ok ? 8 : 0);
-      }
-    }
-    for (int t = 0; t < nb; ++t) {
-      const uint8_t code = p.tb[s.r][t];
-      const int64_t r0 = (int64_t)term_bi(code) * p.hk, c0 = (int64_t)term_bj(code) * p.hn;
-#pragma unroll
-      for (int q = 0; q < (BN * BK) / NT; ++q) {
-        const int e = tid + q * NT;
-        const int kk = e / BN, jj = e - (e / BN) * BN;
-        const int64_t lk = (int64_t)s.ks * BK + kk, lj = (int64_t)s.tn * BN + jj;
-        const int64_t gr = r0 + lk, gc = c0 + lj;
-        const bool ok = lk < p.hk && lj < p.hn && gr < p.b_rows && gc < p.b_cols;
-        const double* src = ok ? p.B + gr * p.ldb + gc : p.B;
-        cp_async8(rb + (t * BK + kk) * BN + jj, src, ok ? 8 : 0);
-      }
-    }
-  };
+  if (tid >= kConsumers) {
+    // ======================= producers =======================
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kProducerRegs));
+    const int pt = tid - kConsumers;
+    Cursor cl = cur;  // load cursor (one step ahead of the sum cursor)
 
-  // Operand sums of step j: summed tile = sum_t sign_t * source tile t.
-  auto sum_step = [&](int64_t j) {
-    const Step s = decode(p, beg, end, j);
-    const int slot = (int)(j % NS);
-    const double* ra = rawA + slot * C_::kRawA;
-    const double* rb = rawB + slot * C_::kRawB;
-    double* sa = sumA + (int)(j & 1) * BK * BM;
-    double* sb = sumB + (int)(j & 1) * BK * BN;
-    const int na = min((int)p.na[s.r], MAXT), nb = min((int)p.nb[s.r], MAXT);
+    auto issue = [&](const Cursor& c, int slot) {
+      const ProbDesc& d = desc_of<BATCHED>(a, c.p);
+      const int row = d.plan_row + c.r;
+      const int na = min((int)c_plans.na[row], MAXT), nb = min((int)c_plans.nb[row], MAXT);
+      const int tm = c.t / d.tiles_n, tn = c.t - (c.t / d.tiles_n) * d.tiles_n;
+      double* ra = rawA + slot * S::kRawA;
+      double* rb = rawB + slot * S::kRawB;
+      if (d.use_tma) {
+        if (pt == 0) {
+          mbar_arrive_expect_tx(&raw_full[slot], (uint32_t)((na * BM * BK + nb * BK * BN) * sizeof(double)));
+          for (int t = 0; t < na; ++t) {
+            const uint8_t code = c_plans.ta[row][t];
+            tma_load_2d(ra + t * BM * BK, &d.tmA, (int)(term_bj(code) * d.hk + (int64_t)c.ks * BK),
+                        (int)(term_bi(code) * d.hm + (int64_t)tm * BM), &raw_full[slot]);
+          }
+          for (int t = 0; t < nb; ++t) {
+            const uint8_t code = c_plans.tb[row][t];
+            tma_load_2d(rb + t * BK * BN, &d.tmB, (int)(term_bj(code) * d.hn + (int64_t)tn * BN),
+                        (int)(term_bi(code) * d.hk + (int64_t)c.ks * BK), &raw_full[slot]);
+          }
+        } else {
+          mbar_arrive(&raw_full[slot]);
+        }
+      } else {
+        for (int t = 0; t < na; ++t) {
+          const uint8_t code = c_plans.ta[row][t];
+          const int64_t r0 = (int64_t)term_bi(code) * d.hm, c0 = (int64_t)term_bj(code) * d.hk;
 #pragma unroll
-    for (int q = 0; q < (BM * BK) / NT; ++q) {
-      const int e = tid + q * NT;
-      double v = flip_sign(ra[e], term_neg(p.ta[s.r][0]));
-      for (int t = 1; t < na; ++t) {
-        const double x = ra[t * BK * BM + e];
-        v = term_neg(p.ta[s.r][t]) ? v - x : v + x;
-      }
-      sa[e] = v;
-    }
+          for (int q = 0; q < (BM * BK) / kProducers; ++q) {
+            const int e = pt + q * kProducers;
+            const int i = e / BK, kk = e - (e / BK) * BK;
+            const int64_t li = (int64_t)tm * BM + i, lk = (int64_t)c.ks * BK + kk;
+            const int64_t gr = r0 + li, gc = c0 + lk;
+            const bool ok = li < d.hm && lk < d.hk && gr < d.a_rows && gc < d.a_cols;
+            cp_async8(ra + t * BM * BK + e, ok ? d.A + gr * d.lda + gc : d.A, ok ? 8 : 0);
+          }
+        }
+        for (int t = 0; t < nb; ++t) {
+          const uint8_t code = c_plans.tb[row][t];
+          const int64_t r0 = (int64_t)term_bi(code) * d.hk, c0 = (int64_t)term_bj(code) * d.hn;
 #pragma unroll
-    for (int q = 0; q < (BN * BK) / NT; ++q) {
-      const int e = tid + q * NT;
-      double v = flip_sign(rb[e], term_neg(p.tb[s.r][0]));
-      for (int t = 1; t < nb; ++t) {
-        const double x = rb[t * BK * BN + e];
-        v = term_neg(p.tb[s.r][t]) ? v - x : v + x;
+          for (int q = 0; q < (BN * BK) / kProducers; ++q) {
+            const int e = pt + q * kProducers;
+            const int kk = e / BN, jj = e - (e / BN) * BN;
+            const int64_t lk = (int64_t)c.ks * BK + kk, lj = (int64_t)tn * BN + jj;
+            const int64_t gr = r0 + lk, gc = c0 + lj;
+            const bool ok = lk < d.hk && lj < d.hn && gr < d.b_rows && gc < d.b_cols;
+            cp_async8(rb + t * BK * BN + e, ok ? d.B + gr * d.ldb + gc : d.B, ok ? 8 : 0);
+          }
+        }
+        cp_async_mbar_arrive(&raw_full[slot]);
       }
-      sb[e] = v;
-    }
-  };
+    };
 
-  // Register tile: rows {ty*TM/2 + i, BM/2 + ty*TM/2 + i}, cols likewise.
+    issue(cl, 0);
+    cursor_next<BATCHED>(a, cl);
+    int64_t issued = 1, landed = 0;
+    bool timed_out = false;
+    for (int64_t s = 0; s < count && !timed_out; ++s) {
+      if (s + 1 < count) {
+        const int slot1 = (int)((s + 1) % NR);
+        const int64_t use1 = (s + 1) / NR;
+        if (use1 > 0 && !mbar_wait(&raw_empty[slot1], (uint32_t)((use1 - 1) & 1))) {
+          timed_out = true;
+          break;
+        }
+        issue(cl, slot1);
+        ++issued;
+        cursor_next<BATCHED>(a, cl);
+      }
+      const int slot = (int)(s % NR);
+      const int q = (int)(s % NS);
+      if (!mbar_wait(&raw_full[slot], (uint32_t)((s / NR) & 1))) {
+        timed_out = true;
+        break;
+      }
+      ++landed;
+      if (s >= NS && !mbar_wait(&sum_empty[q], (uint32_t)(((s / NS) - 1) & 1))) {
+        timed_out = true;
+        break;
+      }
+      // Operand sums of this k-step, masked to the block's k extent.
+      const ProbDesc& d = desc_of<BATCHED>(a, cur.p);
+      const int row = d.plan_row + cur.r;
+      const int na = min((int)c_plans.na[row], MAXT), nb = min((int)c_plans.nb[row], MAXT);
+      const double* ra = rawA + slot * S::kRawA;
+      const double* rb = rawB + slot * S::kRawB;
+      double* sa = sumA + q * BK * BM;
+      double* sb = sumB + q * BK * BN;
+      const int64_t k0 = (int64_t)cur.ks * BK;
+#pragma unroll
+      for (int qq = 0; qq < (BM * BK) / kProducers; ++qq) {
+        const int e = pt + qq * kProducers;
+        const int kk = e / BM, i = e - (e / BM) * BM;
+        double v = 0.0;
+        if (k0 + kk < d.hk) {
+          const int src = i * BK + kk;
+          v = flip_sign(ra[src], term_neg(c_plans.ta[row][0]));
+          for (int t = 1; t < na; ++t) {
+            const double x = ra[t * BM * BK + src];
+            v = term_neg(c_plans.ta[row][t]) ? v - x : v + x;
+          }
+        }
+        sa[e] = v;
+      }
+#pragma unroll
+      for (int qq = 0; qq < (BN * BK) / kProducers; ++qq) {
+        const int e = pt + qq * kProducers;
+        const int kk = e / BN;
+        double v = 0.0;
+        if (k0 + kk < d.hk) {
+          v = flip_sign(rb[e], term_neg(c_plans.tb[row][0]));
+          for (int t = 1; t < nb; ++t) {
+            const double x = rb[t * BK * BN + e];
+            v = term_neg(c_plans.tb[row][t]) ? v - x : v + x;
+          }
+        }
+        sb[e] = v;
+      }
+      mbar_arrive(&sum_full[q]);
+      mbar_arrive(&raw_empty[slot]);
+      cursor_next<BATCHED>(a, cur);
+    }
+    if (timed_out) {
+      record_timeout();
+      // Let the copies this block still has in flight land (bounded) before leaving.
+      for (int64_t s2 = landed; s2 < issued; ++s2) mbar_wait(&raw_full[s2 % NR], (uint32_t)((s2 / NR) & 1));
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    return;
+  }
+
+  // ======================= consumers =======================
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kConsumerRegs));
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   double acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int jn = 0; jn < TN; ++jn) acc[i][jn] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
-  auto row_of = [&](int i) { return (i < TM / 2) ? ty * (TM / 2) + i : BM / 2 + ty * (TM / 2) + (i - TM / 2); };
-  auto col_of = [&](int jn) { return (jn < TN / 2) ? tx * (TN / 2) + jn : BN / 2 + tx * (TN / 2) + (jn - TN / 2); };
-
-  auto epilogue = [&](const Step& s) {
-    const int nc = p.nc[s.r];
-    for (int t = 0; t < nc; ++t) {
-      const uint8_t code = p.tc[s.r][t];
-      const int neg = term_neg(code);
-      const int64_t r0 = (int64_t)term_bi(code) * p.hm, c0 = (int64_t)term_bj(code) * p.hn;
-#pragma unroll
-      for (int i = 0; i < TM; ++i) {
-        const int64_t li = (int64_t)s.tm * BM + row_of(i);
-        const int64_t gr = r0 + li;
-        if (li >= p.hm || gr >= p.c_rows) continue;
-        double* crow = p.C + gr * p.ldc;
-#pragma unroll
-        for (int jn = 0; jn < TN; ++jn) {
-          const int64_t lj = (int64_t)s.tn * BN + col_of(jn);
-          const int64_t gc = c0 + lj;
-          if (lj >= p.hn || gc >= p.c_cols) continue;
-          if (p.epi == kEpiAtomicAdd) {
-            atomicAdd(crow + gc, flip_sign(acc[i][jn], neg));
-          } else if (p.epi == kEpiRmw) {
-            crow[gc] = neg ? crow[gc] - acc[i][jn] : crow[gc] + acc[i][jn];
-          } else {
-            crow[gc] = flip_sign(acc[i][jn], neg);
-          }
-        }
-      }
+  for (int64_t s = 0; s < count; ++s) {
+    const int q = (int)(s % NS);
+    if (!mbar_wait(&sum_full[q], (uint32_t)((s / NS) & 1))) {
+      record_timeout();
+      return;
     }
-#pragma unroll
-    for (int i = 0; i < TM; ++i)
-#pragma unroll
-      for (int jn = 0; jn < TN; ++jn) acc[i][jn] = 0.0;
-  };
-
-  // Prologue: fill NS-1 ring slots, then form the sums of step 0.
-#pragma unroll
-  for (int q = 0; q < NS - 1; ++q) {
-    if (q < count) load_step(q);
-    cp_async_commit();
-  }
-  cp_async_wait<NS - 2>();
-  __syncthreads();
-  sum_step(0);
-
-  for (int64_t j = 0; j < count; ++j) {
-    if (j + NS - 1 < count) load_step(j + NS - 1);
-    cp_async_commit();
-    cp_async_wait<NS - 2>();  // step j+1 has landed (this thread's copies)
-    __syncthreads();          // ... everyone's; summed[j&1] complete; summed[(j+1)&1] free
-    if (j + 1 < count) sum_step(j + 1);
-    const double* sa = sumA + (int)(j & 1) * BK * BM;
-    const double* sb = sumB + (int)(j & 1) * BK * BN;
-#pragma unroll
+    const double* sa = sumA + q * BK * BM;
+    const double* sb = sumB + q * BK * BN;
+    // One k at a time: 64 independent FMAs per k already cover the FP64 pipe's
+    // latency, and not unrolling keeps the register tile free of hoisted fragments.
+#pragma unroll 1
     for (int kk = 0; kk < BK; ++kk) {
-      double a[TM], b[TN];
+      double av[TM], bv[TN];
       const double2* pa0 = reinterpret_cast<const double2*>(sa + kk * BM + ty * (TM / 2));
       const double2* pa1 = reinterpret_cast<const double2*>(sa + kk * BM + BM / 2 + ty * (TM / 2));
       const double2* pb0 = reinterpret_cast<const double2*>(sb + kk * BN + tx * (TN / 2));
@@ -266,196 +435,288 @@ fp64_strassen_kernel(const __grid_constant__ KParams p) {
 #pragma unroll
       for (int v = 0; v < TM / 4; ++v) {
         const double2 x0 = pa0[v], x1 = pa1[v];
-        a[2 * v] = x0.x; a[2 * v + 1] = x0.y;
-        a[TM / 2 + 2 * v] = x1.x; a[TM / 2 + 2 * v + 1] = x1.y;
+        av[2 * v] = x0.x; av[2 * v + 1] = x0.y;
+        av[TM / 2 + 2 * v] = x1.x; av[TM / 2 + 2 * v + 1] = x1.y;
       }
 #pragma unroll
       for (int v = 0; v < TN / 4; ++v) {
         const double2 y0 = pb0[v], y1 = pb1[v];
-        b[2 * v] = y0.x; b[2 * v + 1] = y0.y;
-        b[TN / 2 + 2 * v] = y1.x; b[TN / 2 + 2 * v + 1] = y1.y;
+        bv[2 * v] = y0.x; bv[2 * v + 1] = y0.y;
+        bv[TN / 2 + 2 * v] = y1.x; bv[TN / 2 + 2 * v + 1] = y1.y;
       }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int jn = 0; jn < TN; ++jn) acc[i][jn] = fma(a[i], b[jn], acc[i][jn]);
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
-    const Step s = decode(p, beg, end, j);
-    if (s.last) epilogue(s);
+    mbar_arrive(&sum_empty[q]);
+
+    if (cursor_last<BATCHED>(a, cur)) {
+      // Scatter epilogue: C_q += gamma_q * M_tile for every target of the product.
+      // The tile leaves the registers one row group at a time through a per-warp
+      // staging buffer, so that each warp issues coalesced atomics over whole tile rows
+      // (and the register tile is not held twice).
+      const ProbDesc& d = desc_of<BATCHED>(a, cur.p);
+      const int row = d.plan_row + cur.r;
+      const int nc = d.m_target ? 1 : (int)c_plans.nc[row];
+      const int tm = cur.t / d.tiles_n, tn = cur.t - (cur.t / d.tiles_n) * d.tiles_n;
+      const int warp = tid >> 5, lane = tid & 31;
+      double* stage = epi_stage + warp * (2 * BN);
+      const int half = ty - 2 * warp;  // which of the warp's two thread rows
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        double2* dst0 = reinterpret_cast<double2*>(stage + half * BN + tx * (TN / 2));
+        double2* dst1 = reinterpret_cast<double2*>(stage + half * BN + BN / 2 + tx * (TN / 2));
+#pragma unroll
+        for (int v = 0; v < TN / 4; ++v) {
+          dst0[v] = make_double2(acc[i][2 * v], acc[i][2 * v + 1]);
+          dst1[v] = make_double2(acc[i][TN / 2 + 2 * v], acc[i][TN / 2 + 2 * v + 1]);
+        }
+        __syncwarp();
+        // Local tile rows of this row group for the warp's two thread rows.
+        const int rr0 = (i < TM / 2) ? (2 * warp) * (TM / 2) + i : BM / 2 + (2 * warp) * (TM / 2) + (i - TM / 2);
+        const int rr1 = rr0 + TM / 2;
+#pragma unroll 1
+        for (int t = 0; t < nc; ++t) {
+          const uint8_t code = d.m_target ? term_code(0, 0, 0) : c_plans.tc[row][t];
+          const int neg = term_neg(code);
+          const int64_t row0 = (int64_t)term_bi(code) * d.hm + (int64_t)tm * BM;
+          const int64_t col0 = (int64_t)term_bj(code) * d.hn + (int64_t)tn * BN;
+          const int64_t row_lim = min(d.hm - (int64_t)tm * BM, d.c_rows - row0);
+          const int64_t col_lim = min(d.hn - (int64_t)tn * BN, d.c_cols - col0);
+#pragma unroll
+          for (int q = 0; q < (2 * BN) / 32; ++q) {
+            const int e = lane + 32 * q;
+            const int h = e / BN, col = e - (e / BN) * BN;
+            const int rr = h ? rr1 : rr0;
+            if (rr < row_lim && col < col_lim)
+              // red.global.add.f64, performed in the L2 (off the FP64 pipe).  Each C
+              // element of a tile is always updated by the same thread, in product
+              // order, so one owner per tile gives a deterministic result.
+              atomicAdd(d.C + (row0 + rr) * d.ldc + col0 + col, flip_sign(stage[e], neg));
+          }
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    }
+    cursor_next<BATCHED>(a, cur);
   }
-  cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- host side
 
-struct TileInfo {
-  int bm, bn, bk, threads, maxt;
-  size_t smem;
-  const void* fn[3];  // by MAXT class: 1, 2, 4 terms
-  int occ[3];
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+struct DeviceState {
+  bool ready = false;
+  cudaError_t err = cudaSuccess;
+  int sms = 0;
 };
+constexpr int kMaxDev = 64;
+DeviceState g_dev[kMaxDev];
+std::mutex g_mu;
 
-template <int BM, int BN, int BK, int TM, int TN, int NS>
-TileInfo make_tile_info() {
-  TileInfo t;
-  t.bm = BM; t.bn = BN; t.bk = BK;
-  t.threads = (BM / TM) * (BN / TN);
-  t.maxt = 4;
-  t.smem = Cfg<BM, BN, BK, TM, TN, 4, NS>::kSmem;
-  t.fn[0] = (const void*)fp64_strassen_kernel<BM, BN, BK, TM, TN, 1, NS>;
-  t.fn[1] = (const void*)fp64_strassen_kernel<BM, BN, BK, TM, TN, 2, NS>;
-  t.fn[2] = (const void*)fp64_strassen_kernel<BM, BN, BK, TM, TN, 4, NS>;
-  t.occ[0] = t.occ[1] = t.occ[2] = 0;
-  return t;
+template <int MAXT, bool BATCHED>
+const void* kernel_fn() {
+  return (const void*)fp64_strassen_kernel<MAXT, BATCHED>;
 }
 
-template <int BM, int BN, int BK, int TM, int TN, int NS>
-size_t smem_for(int cls) {
-  return cls == 0 ? Cfg<BM, BN, BK, TM, TN, 1, NS>::kSmem
-                  : cls == 1 ? Cfg<BM, BN, BK, TM, TN, 2, NS>::kSmem : Cfg<BM, BN, BK, TM, TN, 4, NS>::kSmem;
+const void* pick_kernel(int maxt_class, bool batched) {
+  if (batched) return maxt_class == 0 ? kernel_fn<1, true>() : maxt_class == 1 ? kernel_fn<2, true>() : kernel_fn<4, true>();
+  return maxt_class == 0 ? kernel_fn<1, false>() : maxt_class == 1 ? kernel_fn<2, false>() : kernel_fn<4, false>();
+}
+size_t smem_bytes(int maxt_class) {
+  return maxt_class == 0 ? Smem<1>::kBytes : maxt_class == 1 ? Smem<2>::kBytes : Smem<4>::kBytes;
 }
 
-constexpr int kNumTiles = 2;
-// Tile 0: 128x128 block tile, 8x8 per thread, 256 threads.  Tile 1: 64x64, 4x4.
-TileInfo g_tiles[kNumTiles];
-size_t g_smem[kNumTiles][3];
-std::once_flag g_once;
-int g_sms = 0;
-cudaError_t g_init_err = cudaSuccess;
-
-void init_tiles() {
-  g_tiles[0] = make_tile_info<128, 128, 4, 8, 8, 3>();
-  g_tiles[1] = make_tile_info<64, 64, 4, 4, 4, 3>();
-  for (int c = 0; c < 3; ++c) {
-    g_smem[0][c] = smem_for<128, 128, 4, 8, 8, 3>(c);
-    g_smem[1][c] = smem_for<64, 64, 4, 4, 4, 3>(c);
-  }
+cudaError_t ensure_device(int* sms_out) {
   int dev = 0;
-  g_init_err = cudaGetDevice(&dev);
-  if (g_init_err != cudaSuccess) return;
-  g_init_err = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (g_init_err != cudaSuccess) return;
-  for (int t = 0; t < kNumTiles; ++t)
-    for (int c = 0; c < 3; ++c) {
-      g_init_err = cudaFuncSetAttribute(g_tiles[t].fn[c], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)g_smem[t][c]);
-      if (g_init_err != cudaSuccess) return;
-      int occ = 0;
-      g_init_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g_tiles[t].fn[c],
-                                                                 g_tiles[t].threads, g_smem[t][c]);
-      if (g_init_err != cudaSuccess) return;
-      g_tiles[t].occ[c] = std::max(occ, 1);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState& st = g_dev[dev];
+  if (!st.ready) {
+    st.ready = true;
+    st.err = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int c = 0; c < 3 && st.err == cudaSuccess; ++c)
+      for (int b = 0; b < 2 && st.err == cudaSuccess; ++b)
+        st.err = cudaFuncSetAttribute(pick_kernel(c, b != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_bytes(c));
+    if (!g_encode && st.err == cudaSuccess) {
+      cudaDriverEntryPointQueryResult q;
+      void* fn = nullptr;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+              cudaSuccess &&
+          q == cudaDriverEntryPointSuccess)
+        g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+      else
+        cudaGetLastError();  // no TMA descriptors: every problem takes the cp.async path
     }
+  }
+  *sms_out = st.sms;
+  return st.err;
 }
 
-int term_class(const Plan& pl, int only) {
+int term_class_of(int levels, int prod_begin, int nprod) {
   int mx = 1;
-  for (int r = 0; r < pl.nprod; ++r) {
-    if (only >= 0 && r != only) continue;
-    mx = std::max(mx, (int)std::max(pl.na[r], pl.nb[r]));
+  for (int r = prod_begin; r < prod_begin + nprod; ++r) {
+    const int row = kPlanOffset[levels] + r;
+    mx = std::max(mx, (int)std::max(kPlanTables.na[row], kPlanTables.nb[row]));
   }
   return mx <= 1 ? 0 : (mx <= 2 ? 1 : 2);
 }
 
-}  // namespace
-
-int fp64_num_tiles() { return kNumTiles; }
-
-int device_sm_count() {
-  std::call_once(g_once, init_tiles);
-  return g_sms;
+bool encode_2d(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+               int box_rows) {
+  if (!g_encode) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(double))};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, (void*)base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
-// Estimated cost (FP64-pipe cycles summed over SMs, arbitrary units) of running the
-// launch with tile t and schedule `sched`, counting padded-tile FMAs, operand-sum adds
-// (about 1.2 FMA each, measured) and the wave quantisation of owner scheduling.
-static double estimate(const Fp64Launch& L, int t, int sched, int nprod, double avg_extra_terms) {
-  const TileInfo& ti = g_tiles[t];
-  const int64_t tiles_m = (L.hm + ti.bm - 1) / ti.bm, tiles_n = (L.hn + ti.bn - 1) / ti.bn;
-  const int64_t ksteps = (L.hk + ti.bk - 1) / ti.bk;
-  const double fma_per_unit = (double)ti.bm * ti.bn * ti.bk * ksteps;
-  const double add_per_unit = 1.2 * avg_extra_terms * (double)(ti.bm + ti.bn) * ti.bk * ksteps;
-  const double unit = fma_per_unit + add_per_unit;
-  const double slots = (double)g_sms;  // the FP64 pipe is per SM: balance over SMs
-  const double units = (double)nprod * tiles_m * tiles_n;
-  if (sched == kSchedStreamK) return unit * units / slots;
-  const double positions = (double)tiles_m * tiles_n;
-  return unit * nprod * std::ceil(positions / slots);
+// Fills a device descriptor from a launch.  TMA is used when every box coordinate the
+// kernel will issue is 16-byte aligned in the innermost dimension and the operands'
+// base addresses and row strides are 16-byte multiples.
+void fill_desc(const Fp64Launch& L, ProbDesc* d) {
+  std::memset(d, 0, sizeof(*d));
+  d->A = L.A; d->B = L.B; d->C = L.C;
+  d->lda = L.lda; d->ldb = L.ldb; d->ldc = L.ldc;
+  d->a_rows = L.a_rows; d->a_cols = L.a_cols; d->b_rows = L.b_rows; d->b_cols = L.b_cols;
+  d->c_rows = L.c_rows; d->c_cols = L.c_cols;
+  d->hm = L.hm; d->hn = L.hn; d->hk = L.hk;
+  const int nprod = L.nprod < 0 ? kPlanCount[L.levels] - L.prod_begin : L.nprod;
+  d->plan_row = kPlanOffset[L.levels] + L.prod_begin;
+  d->nprod = nprod;
+  d->m_target = L.m_target;
+  d->epi = L.epi;
+  d->tiles_m = (int)((L.hm + BM - 1) / BM);
+  d->tiles_n = (int)((L.hn + BN - 1) / BN);
+  d->ksteps = (int)((L.hk + BK - 1) / BK);
+  const bool aligned = ((uintptr_t)L.A % 16 == 0) && ((uintptr_t)L.B % 16 == 0) && (L.lda % 2 == 0) &&
+                       (L.ldb % 2 == 0) && (L.levels == 0 || (L.hk % 2 == 0 && L.hn % 2 == 0)) &&
+                       L.a_cols < (1LL << 31) && L.a_rows < (1LL << 31) && L.b_cols < (1LL << 31) &&
+                       L.b_rows < (1LL << 31);
+  d->use_tma = aligned && encode_2d(&d->tmA, L.A, L.a_rows, L.a_cols, L.lda, BK, BM) &&
+               encode_2d(&d->tmB, L.B, L.b_rows, L.b_cols, L.ldb, BN, BK);
+}
+
+}  // namespace
+
+int device_sm_count() {
+  int sms = 0;
+  ensure_device(&sms);
+  return sms;
+}
+
+// Estimated FP64-pipe time (arbitrary units) of a schedule: padded-tile FMAs, operand
+// sums (off the critical path in the producer warps, counted at a quarter) and the
+// wave quantisation of owner scheduling.
+static double estimate(const Fp64Launch& L, int sched, int nprod, int sms) {
+  const double tiles_m = (double)((L.hm + BM - 1) / BM), tiles_n = (double)((L.hn + BN - 1) / BN);
+  const double ksteps = (double)((L.hk + BK - 1) / BK);
+  const double unit = (double)BM * BN * BK * ksteps;
+  if (sched == kSchedStreamK) return unit * nprod * tiles_m * tiles_n / sms;
+  return unit * nprod * std::ceil(tiles_m * tiles_n / sms);
 }
 
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic) {
-  std::call_once(g_once, init_tiles);
-  const Plan& pl = *L->plan;
-  int nprod = L->only_product >= 0 ? 1 : pl.nprod;
-  double extra = 0;
-  for (int r = 0; r < pl.nprod; ++r) {
-    if (L->only_product >= 0 && r != L->only_product) continue;
-    extra += (pl.na[r] - 1) * 0.5 + (pl.nb[r] - 1) * 0.5;
-  }
-  extra /= nprod;
-  double best = 1e300;
-  int bt = 0, bs = kSchedOwner;
-  for (int t = 0; t < kNumTiles; ++t)
-    for (int s = 0; s < 2; ++s) {
-      if (prefer_deterministic && s == kSchedStreamK) continue;
-      // Stream-K needs atomic accumulation; a plain store epilogue cannot use it.
-      if (s == kSchedStreamK && L->epi == kEpiStore) continue;
-      // Owner scheduling pays full waves; prefer it (deterministic) within 2%.
-      const double c = estimate(*L, t, s, nprod, extra) * (s == kSchedOwner ? 0.98 : 1.0);
-      if (c < best) { best = c; bt = t; bs = s; }
-    }
-  L->tile = bt;
-  L->sched = (ScheduleKind)bs;
-  if (bs == kSchedStreamK) L->epi = kEpiAtomicAdd;
-  else if (L->epi == kEpiAtomicAdd) L->epi = kEpiRmw;
+  int sms = 0;
+  ensure_device(&sms);
+  if (sms <= 0) sms = 1;
+  const int nprod = L->nprod < 0 ? kPlanCount[L->levels] - L->prod_begin : L->nprod;
+  const double so = estimate(*L, kSchedOwner, nprod, sms);
+  const double ss = estimate(*L, kSchedStreamK, nprod, sms);
+  // Owner scheduling is deterministic (one writer per C tile, fixed product order):
+  // keep it unless stream-K is more than 3% faster by the estimate.
+  const bool owner = prefer_deterministic || so <= ss * 1.03;
+  L->tile = 0;
+  L->sched = owner ? kSchedOwner : kSchedStreamK;
 }
 
 cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream) {
-  std::call_once(g_once, init_tiles);
-  if (g_init_err != cudaSuccess) return g_init_err;
-  if (L.tile < 0 || L.tile >= kNumTiles) return cudaErrorInvalidValue;
-  const TileInfo& ti = g_tiles[L.tile];
-  const Plan& pl = *L.plan;
-  KParams p;
-  std::memset(&p, 0, sizeof(p));
-  p.A = L.A; p.B = L.B; p.C = L.C;
-  p.lda = L.lda; p.ldb = L.ldb; p.ldc = L.ldc;
-  p.a_rows = L.a_rows; p.a_cols = L.a_cols;
-  p.b_rows = L.b_rows; p.b_cols = L.b_cols;
-  p.c_rows = L.c_rows; p.c_cols = L.c_cols;
-  p.hm = L.hm; p.hn = L.hn; p.hk = L.hk;
-  int np = 0;
-  for (int r = 0; r < pl.nprod; ++r) {
-    if (L.only_product >= 0 && r != L.only_product) continue;
-    p.na[np] = pl.na[r]; p.nb[np] = pl.nb[r]; p.nc[np] = pl.nc[r];
-    std::memcpy(p.ta[np], pl.ta[r], kMaxTerms);
-    std::memcpy(p.tb[np], pl.tb[r], kMaxTerms);
-    std::memcpy(p.tc[np], pl.tc[r], kMaxTerms);
-    ++np;
-  }
-  if (np == 0) return cudaErrorInvalidValue;
-  p.nprod = np;
-  p.tiles_m = (int)((L.hm + ti.bm - 1) / ti.bm);
-  p.tiles_n = (int)((L.hn + ti.bn - 1) / ti.bn);
-  p.ksteps = (int)((L.hk + ti.bk - 1) / ti.bk);
-  p.epi = L.epi;
-  p.sched = L.sched;
-  if (L.sched == kSchedStreamK && L.epi != kEpiAtomicAdd) return cudaErrorInvalidValue;
-  const int cls = term_class(pl, L.only_product);
-  const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
+  int sms = 0;
+  cudaError_t e = ensure_device(&sms);
+  if (e != cudaSuccess) return e;
+  if (L.levels < 0 || L.levels > 2) return cudaErrorInvalidValue;
+  KArgs args;
+  std::memset(&args, 0, sizeof(args));
+  fill_desc(L, &args.single);
+  const ProbDesc& d = args.single;
+  if (d.nprod <= 0 || d.ksteps <= 0 || d.tiles_m <= 0 || d.tiles_n <= 0) return cudaSuccess;
+  args.nprob = 1;
+  args.sched = L.sched;
+  const int64_t tiles = (int64_t)d.tiles_m * d.tiles_n;
   int64_t grid;
-  const int64_t resident = (int64_t)g_sms * ti.occ[cls];
   if (L.sched == kSchedStreamK) {
-    p.total = (int64_t)np * tiles * p.ksteps;
-    grid = std::min<int64_t>(resident, p.total);
+    args.total = (int64_t)d.nprod * tiles * d.ksteps;
+    grid = std::min<int64_t>(sms, args.total);
   } else {
-    p.total = tiles;
-    grid = std::min<int64_t>(resident, tiles);
+    args.total = tiles;
+    grid = std::min<int64_t>(sms, tiles);
   }
-  if (grid <= 0) return cudaSuccess;
-  void* args[] = {&p};
-  return cudaLaunchKernel(ti.fn[cls], dim3((unsigned)grid), dim3(ti.threads), args, g_smem[L.tile][cls],
+  const int cls = term_class_of(L.levels, L.prod_begin, d.nprod);
+  void* kargs[] = {&args};
+  return cudaLaunchKernel(pick_kernel(cls, false), dim3((unsigned)grid), dim3(kThreads), kargs, smem_bytes(cls),
                           stream);
+}
+
+size_t fp64_batched_scratch_bytes(int count) { return sizeof(ProbDesc) * (size_t)std::max(count, 1); }
+
+cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratch, cudaStream_t stream) {
+  int sms = 0;
+  cudaError_t e = ensure_device(&sms);
+  if (e != cudaSuccess) return e;
+  std::vector<ProbDesc> descs;
+  descs.reserve(count);
+  int64_t total = 0;
+  int cls = 0;
+  for (int i = 0; i < count; ++i) {
+    ProbDesc d;
+    Fp64Launch L = probs[i];
+    L.epi = kEpiAtomicAdd;
+    L.sched = kSchedStreamK;
+    fill_desc(L, &d);
+    if (d.nprod <= 0 || d.ksteps <= 0 || d.tiles_m <= 0 || d.tiles_n <= 0) continue;
+    d.iter_begin = total;
+    total += (int64_t)d.nprod * d.tiles_m * d.tiles_n * d.ksteps;
+    cls = std::max(cls, term_class_of(L.levels, L.prod_begin, d.nprod));
+    descs.push_back(d);
+  }
+  if (descs.empty()) return cudaSuccess;
+  e = cudaMemcpyAsync(scratch, descs.data(), sizeof(ProbDesc) * descs.size(), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return e;
+  // The host vector must outlive the copy: pageable memcpy is staged before return.
+  KArgs args;
+  std::memset(&args, 0, sizeof(args));
+  args.descs = (const ProbDesc*)scratch;
+  args.nprob = (int)descs.size();
+  args.sched = kSchedStreamK;
+  args.total = total;
+  const int64_t grid = std::min<int64_t>(sms, total);
+  void* kargs[] = {&args};
+  return cudaLaunchKernel(pick_kernel(cls, true), dim3((unsigned)grid), dim3(kThreads), kargs, smem_bytes(cls),
+                          stream);
+}
+
+int fp64_device_status(cudaStream_t stream) {
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fp64_status, sizeof(int)) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  if (v != 0) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_fp64_status, &zero, sizeof(int)) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  }
+  return v;
 }
 
 }  // namespace sgb

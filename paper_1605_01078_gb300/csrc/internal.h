@@ -5,24 +5,13 @@
 #include <stdint.h>
 
 #include "../../include/strassen.h"
+#include "plan_tables.h"
 
 namespace sgb {
 
-// Largest table the kernels take: 7^2 products with 2^2 terms per operand and up to
-// 4 C targets (Eq. 3, Section 3.5).
 constexpr int kMaxProducts = 49;
-constexpr int kMaxTerms = 4;
 
-// One term of a product: block (bi, bj) of the 2^L x 2^L partition with a sign.
-// Encoded in one byte: bits 0-2 block column, bits 3-5 block row, bit 7 negative.
-__host__ __device__ inline uint8_t term_code(int bi, int bj, int neg) {
-  return (uint8_t)((bj & 7) | ((bi & 7) << 3) | (neg ? 0x80 : 0));
-}
-__host__ __device__ inline int term_bj(uint8_t c) { return c & 7; }
-__host__ __device__ inline int term_bi(uint8_t c) { return (c >> 3) & 7; }
-__host__ __device__ inline int term_neg(uint8_t c) { return (c >> 7) & 1; }
-
-// The coefficient table of Eq. 4 for L levels, in the encoding above.
+// Host copy of the table of one level count (rows of kPlanTables).
 struct Plan {
   int levels = 0;
   int nprod = 0;
@@ -30,7 +19,7 @@ struct Plan {
   uint8_t ta[kMaxProducts][kMaxTerms], tb[kMaxProducts][kMaxTerms], tc[kMaxProducts][kMaxTerms];
 };
 
-// Builds the table for levels 0, 1 or 2 (Figure 1 and its Kronecker square).
+// Copies the table for levels 0, 1 or 2 (Figure 1 and its Kronecker square).
 // Returns false for other levels.
 bool make_plan(int levels, Plan* out);
 
@@ -40,11 +29,13 @@ inline int64_t block_edge(int64_t d, int levels) {
   return (d + p - 1) / p;
 }
 
-// How partial products reach C (or the temporary M).
+// What the caller wants done with a product: accumulate into C, or store into a
+// temporary (the kernel always accumulates with device atomics; a store is a clear of
+// the target followed by the adds).
 enum EpilogueKind : int {
-  kEpiAtomicAdd = 0,  // red.global.add.f64 of +/- M into every target (any schedule)
-  kEpiRmw = 1,        // load, add, store: only when one block owns the target tile
-  kEpiStore = 2       // overwrite (AB / Naive temporary M): only when one block owns it
+  kEpiAtomicAdd = 0,  // accumulate, any schedule
+  kEpiRmw = 1,        // accumulate with one owner per tile (deterministic order)
+  kEpiStore = 2       // the target is a temporary that the caller clears first
 };
 
 // How work units are spread over the persistent grid.
@@ -53,7 +44,8 @@ enum ScheduleKind : int {
   kSchedOwner = 1     // each block owns whole tile positions, all products, all of k
 };
 
-// One launch of the FP64 product kernel: all products of a plan over one (A, B, C).
+// One problem for the FP64 product kernel: products [prod_begin, prod_begin + nprod)
+// of the `levels` table over (A, B, C).
 struct Fp64Launch {
   const double* A;
   const double* B;
@@ -63,21 +55,32 @@ struct Fp64Launch {
   int64_t b_rows, b_cols;  // extent of B (k x n)
   int64_t c_rows, c_cols;  // extent of C that may be written (m x n, or hm x hn for M)
   int64_t hm, hn, hk;      // block edges
-  const Plan* plan;        // products to run (all of them, or one via `only_product`)
-  int only_product;        // -1 = all products of the plan, else just this one
+  int levels;
+  int prod_begin, nprod;   // nprod < 0: all products of the level
+  int m_target;            // 1: every product writes block (0,0) of C with sign + (temporary M)
   EpilogueKind epi;
   ScheduleKind sched;
-  int tile;                // tile configuration id (see fp64_gemm.cu)
+  int tile;
 };
 
-// Launches the FP64 product kernel; returns a CUDA error code.
+// Fills the fields common to a full-operand launch.
+Fp64Launch make_launch(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, int levels);
+
+// Launches the FP64 product kernel on one problem; returns a CUDA error code.
 cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream);
 
-// Number of tile configurations the FP64 kernel is built for.
-int fp64_num_tiles();
+// Launches one persistent kernel over `count` problems (all scheduled stream-K with
+// atomic C updates).  `scratch` is device memory of fp64_batched_scratch_bytes(count).
+size_t fp64_batched_scratch_bytes(int count);
+cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratch, cudaStream_t stream);
 
-// Picks a schedule and tile for a launch (balance heuristics for 152 SMs).
+// Picks a schedule for a launch (balance heuristics for the SM count).
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic);
+
+// Reads and clears the device-side status word of the product kernels (set when a
+// bounded wait gave up).  Synchronises `stream` first.
+int fp64_device_status(cudaStream_t stream);
 
 // Naive / AB helpers (elementwise.cu).
 // dst (rows x cols, ld = cols) = sum_t sign_t * block_t of src, masked to src's extent.
