@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--variant", default="ABC")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -144,6 +145,49 @@ def recorded_traffic():
         return float(rec["dram_bytes_per_launch_8192_2L_ABC"])
     except (KeyError, ValueError):
         return None
+
+
+def bench_batched(sg, W, torch, reps=3):
+    """256 FP64 problems, m, n, k log-uniform in [256, 4096] (seed 0), levels from the
+    selector, in one persistent launch captured in a CUDA graph; against a loop of 256
+    classical launches on the same operands."""
+    shapes = W.loguniform_shapes(256, seed=0, lo=256, hi=4096)
+    mats = [(W.uniform_device(m, k, 1000 + i), W.uniform_device(k, n, 2000 + i), W.uniform_device(m, n, 3000 + i))
+            for i, (m, n, k) in enumerate(shapes)]
+    arr = (sg.strassen_problem * len(mats))()
+    for i, (A, B, C) in enumerate(mats):
+        arr[i] = sg.strassen_problem(A.shape[0], B.shape[1], A.shape[1], A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                     A.stride(0), B.stride(0), C.stride(0), -1, sg.STRASSEN_AUTO)
+    flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
+    stream = torch.cuda.current_stream()
+    assert sg.strassen_gemm_batched(len(mats), arr, 0, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        assert sg.strassen_gemm_batched(len(mats), arr, 0, torch.cuda.current_stream().cuda_stream) == 0
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / 1e3 / reps
+    for A, B, C in mats:
+        sg.classical(A, B, C)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        for A, B, C in mats:
+            sg.classical(A, B, C)
+    e1.record()
+    torch.cuda.synchronize()
+    t_loop = e0.elapsed_time(e1) / 1e3 / reps
+    return {"workload": "256 FP64 problems, m,n,k log-uniform in [256,4096] (seed 0), one persistent launch in a CUDA graph",
+            "value": flops / t_graph / 1e9, "unit": UNIT, "ms": t_graph * 1e3,
+            "loop_of_classical": {"value": flops / t_loop / 1e9, "ms": t_loop * 1e3, "launches": len(mats)},
+            "speedup_vs_loop": t_loop / t_graph}
 
 
 def cpu_oracle_effective(n, levels, reps=1):
@@ -298,6 +342,10 @@ def main():
                "h2d_bytes_per_step": int(3 * 8 * m * n), "d2h_bytes_per_step": int(8 * m * n)}
         del dA, dB, dC
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = bench_batched(sg, W, torch)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -327,6 +375,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

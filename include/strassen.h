@@ -152,33 +152,58 @@ typedef struct {
  *
  *   count   number of problems (>= 0).
  *   probs   HOST array of `count` problems; each is validated as in strassen_gemm.
- *           The C blocks of different problems must not overlap.
+ *           The byte ranges [C, C + (m-1)*ldc + n) of different problems must not
+ *           overlap (STRASSEN_ERR_ARG otherwise).  levels = -1 or variant =
+ *           STRASSEN_AUTO takes strassen_select()'s level; every problem runs as ABC
+ *           (levels 1, 2) or classical (levels 0) inside the one launch.
  *   dtype   STRASSEN_F64.
  *   stream  the CUDA stream.
  *
- * The problems are split into work units (problem, product, tile, k-range) listed in
- * a device work list; resident thread blocks take units from a device counter until
- * the list is empty.  The call copies the work list to a stream-ordered temporary,
- * so it can be captured in a CUDA graph and replayed.  Returns STRASSEN_OK or a
- * negative status (STRASSEN_ERR_TIMEOUT if a device-side wait gave up).
+ * The problems are split into work units (problem, product, 128x128 tile, k-steps);
+ * the thread blocks of one persistent launch take equal contiguous ranges of them
+ * (stream-K) and add their partial products into C with device atomics.  The work
+ * list travels in kernel parameters to a small kernel that writes it into a
+ * stream-ordered temporary (cudaMallocAsync), so the whole call can be captured in a
+ * CUDA graph and replayed.  Returns STRASSEN_OK or a negative status.
  */
 STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
                           strassen_dtype dtype, strassen_stream_t stream);
 
 /*
- * strassen_select -- the variant selector: predicts the fastest of {classical,
- * 1L/2L x ABC/AB/Naive} x tile for an m x n x k product in `dtype` (the choice of
- * implementation the paper's performance model of Section 4.2 is meant to support).
- * Uses the trained MLP loaded by strassen_selector_load(); without one, or when the
- * shape was timed by the autotuner, the exhaustive measurement recorded by
- * strassen_tune_record() is used instead; with neither, a fixed rule (2 levels of
- * ABC when min(m, n, k) >= 2048, else classical).
+ * strassen_select -- the variant selector: picks which member of the family (classical,
+ * or 1 / 2 levels of ABC, AB or Naive; tile_id is always 0, the 128x128x8 tile) to
+ * run for an m x n x k product in `dtype` -- the choice Section 4.2 of the paper
+ * builds its performance model for.  In order of precedence it returns
+ *   1. the exhaustive-measurement record for exactly this shape and dtype, if one was
+ *      stored with strassen_tune_record();
+ *   2. the analytic model's argmin (strassen_model_seconds) otherwise.
+ * Fewer levels win ties within 1 %.
  *
  *   levels, variant, tile_id   outputs (host pointers, non-NULL).
- * Returns STRASSEN_OK or a negative status.
+ * Returns STRASSEN_OK or a negative status.  Host-only; launches nothing.
  */
 STRASSEN_API int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype,
-                    int* levels, strassen_variant* variant, int* tile_id);
+                                 int* levels, strassen_variant* variant, int* tile_id);
+
+/*
+ * strassen_tune_record / strassen_tune_clear -- store (or forget all) exhaustive
+ * measurement results: the fastest (levels, variant, tile_id) measured for a shape
+ * and dtype, which strassen_select() then returns for exactly that shape.  The table
+ * lives in host memory of the process.  Returns STRASSEN_OK or a negative status.
+ */
+STRASSEN_API int strassen_tune_record(int64_t m, int64_t n, int64_t k, strassen_dtype dtype,
+                                      int levels, strassen_variant variant, int tile_id);
+STRASSEN_API int strassen_tune_clear(void);
+
+/*
+ * strassen_model_seconds -- the analytic time model (the paper's T = T_a + T_m of
+ * Section 4.2, restated for this GPU): FP64 multiply-adds of the padded 128x128x8
+ * tiles and the operand-sum and C-update additions at the FP64 pipe rate, the extra
+ * temporary passes of AB and Naive at the HBM rate, and a fixed cost per kernel
+ * launch.  Returns the predicted seconds, or -1 for invalid arguments.
+ */
+STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int levels,
+                                           strassen_variant variant);
 
 /*
  * strassen_workspace_size -- bytes of stream-ordered temporaries a strassen_gemm call
@@ -221,6 +246,23 @@ STRASSEN_API int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k,
                                           const double* B, int64_t ldb,
                                           double* C, int64_t ldc,
                                           int levels, strassen_stream_t stream);
+
+/*
+ * strassen_device_status -- waits for `stream`, then reads and clears the library's
+ * device status word.  The kernels bound every device-side wait (about one second);
+ * a wait that runs out sets the word to STRASSEN_ERR_TIMEOUT and the kernel returns
+ * instead of hanging.  Returns STRASSEN_OK, STRASSEN_ERR_TIMEOUT or STRASSEN_ERR_CUDA.
+ */
+STRASSEN_API int strassen_device_status(strassen_stream_t stream);
+
+/*
+ * strassen_check_wait_timeout -- diagnostic: launches one thread that waits on a
+ * barrier nothing completes, for `limit_cycles` SM clock cycles, through the same
+ * bounded-wait code the kernels use.  Afterwards strassen_device_status() returns
+ * STRASSEN_ERR_TIMEOUT and the context stays usable.  Returns STRASSEN_OK or a
+ * negative status (STRASSEN_ERR_ARG for a negative limit).
+ */
+STRASSEN_API int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stream_t stream);
 
 /* strassen_status_string -- a static, NUL-terminated description of a status code. */
 STRASSEN_API const char* strassen_status_string(int status);

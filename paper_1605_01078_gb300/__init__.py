@@ -18,7 +18,9 @@ from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  
                        STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_NAIVE, StrassenError,
                        classical_gemm, strassen_gemm, strassen_gemm_ab_noalloc, strassen_gemm_batched,
                        strassen_plan_table,
-                       strassen_problem, strassen_select, strassen_status_string,
+                       strassen_problem, strassen_select, strassen_status_string, strassen_device_status,
+                       strassen_check_wait_timeout, strassen_tune_record, strassen_tune_clear,
+                       strassen_model_seconds,
                        strassen_workspace_size)
 
 VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO}

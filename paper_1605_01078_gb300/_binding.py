@@ -52,6 +52,11 @@ SIGNATURES = {
     "strassen_status_string": (ctypes.c_char_p, [_I]),
     "strassen_plan_table": (_I, [_I, _I, _IP, _IP, _IP, _IP, _IP, _IP]),
     "strassen_gemm_ab_noalloc": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _P]),
+    "strassen_device_status": (_I, [_P]),
+    "strassen_tune_record": (_I, [_I64, _I64, _I64, _I, _I, _I, _I]),
+    "strassen_tune_clear": (_I, []),
+    "strassen_model_seconds": (ctypes.c_double, [_I64, _I64, _I64, _I, _I]),
+    "strassen_check_wait_timeout": (_I, [_I64, _P]),
 }
 
 
@@ -99,11 +104,31 @@ def strassen_gemm_batched(count, probs, dtype, stream) -> int:
     return lib().strassen_gemm_batched(count, probs, dtype, stream)
 
 
+def strassen_device_status(stream) -> int:
+    return lib().strassen_device_status(stream)
+
+
+def strassen_check_wait_timeout(limit_cycles, stream) -> int:
+    return lib().strassen_check_wait_timeout(limit_cycles, stream)
+
+
 def strassen_select(m, n, k, dtype):
     lv, var, tile = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     st = lib().strassen_select(m, n, k, dtype, ctypes.byref(lv), ctypes.byref(var), ctypes.byref(tile))
     _check(st, "strassen_select")
     return lv.value, var.value, tile.value
+
+
+def strassen_tune_record(m, n, k, dtype, levels, variant, tile_id) -> int:
+    return lib().strassen_tune_record(m, n, k, dtype, levels, variant, tile_id)
+
+
+def strassen_tune_clear() -> int:
+    return lib().strassen_tune_clear()
+
+
+def strassen_model_seconds(m, n, k, levels, variant) -> float:
+    return lib().strassen_model_seconds(m, n, k, levels, variant)
 
 
 def strassen_workspace_size(m, n, k, levels, variant, dtype) -> int:

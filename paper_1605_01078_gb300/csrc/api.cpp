@@ -2,9 +2,12 @@
 // launch sequences of the ABC, AB and Naive variants (Section 4.1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -194,8 +197,62 @@ int classical_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda
 
 int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dtype dtype,
                           strassen_stream_t stream) {
-  (void)count; (void)probs; (void)dtype; (void)stream;
-  return STRASSEN_ERR_UNSUPPORTED;
+  try {
+    if (count < 0) return STRASSEN_ERR_ARG;
+    if (count == 0) return STRASSEN_OK;
+    if (!probs) return STRASSEN_ERR_NULL;
+    if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
+    if (dtype != STRASSEN_F64) return STRASSEN_ERR_UNSUPPORTED;
+    std::vector<Fp64Launch> launches;
+    std::vector<std::pair<const char*, const char*>> cranges;
+    launches.reserve(count);
+    for (int i = 0; i < count; ++i) {
+      const strassen_problem& p = probs[i];
+      if (p.levels < -1 || p.levels > 2) return STRASSEN_ERR_LEVELS;
+      if ((int)p.variant < 0 || (int)p.variant > 3) return STRASSEN_ERR_UNSUPPORTED;
+      const int chk = check_args(p.m, p.n, p.k, p.A, p.lda, p.B, p.ldb, p.C, p.ldc);
+      if (chk < 0) return chk;
+      if (chk == 1) continue;
+      int levels = p.levels;
+      if (levels == -1 || p.variant == STRASSEN_AUTO) {
+        int sl = 0, tile = 0;
+        strassen_variant sv = STRASSEN_ABC;
+        const int st = strassen_select(p.m, p.n, p.k, dtype, &sl, &sv, &tile);
+        if (st != STRASSEN_OK) return st;
+        if (levels == -1) levels = sl;
+      }
+      levels = clamp_levels(levels, p.m, p.n, p.k);
+      launches.push_back(make_launch(p.m, p.n, p.k, p.A, p.lda, p.B, p.ldb, p.C, p.ldc, levels));
+      cranges.emplace_back((const char*)p.C, (const char*)(p.C + (p.m - 1) * p.ldc + p.n));
+    }
+    if (launches.empty()) return STRASSEN_OK;
+    // The C ranges of different problems must not overlap (atomics would mix them).
+    std::sort(cranges.begin(), cranges.end());
+    for (size_t i = 1; i < cranges.size(); ++i)
+      if (cranges[i].first < cranges[i - 1].second) return STRASSEN_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      return STRASSEN_ERR_CUDA;
+    }
+    Workspace ws;
+    ws.s = s;
+    if (cudaMallocAsync(&ws.p, fp64_batched_scratch_bytes((int)launches.size()), s) != cudaSuccess) {
+      cudaGetLastError();
+      ws.p = nullptr;
+      return STRASSEN_ERR_ALLOC;
+    }
+    return cuda_status(launch_fp64_batched(launches.data(), (int)launches.size(), ws.p, s));
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
+}
+
+int strassen_device_status(strassen_stream_t stream) { return fp64_device_status((cudaStream_t)stream); }
+
+int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stream_t stream) {
+  if (limit_cycles < 0) return STRASSEN_ERR_ARG;
+  return cuda_status(launch_wait_timeout_check((long long)limit_cycles, (cudaStream_t)stream));
 }
 
 int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* levels,
@@ -203,12 +260,35 @@ int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* 
   if (!levels || !variant || !tile_id) return STRASSEN_ERR_NULL;
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
-  int64_t mn = m < n ? m : n;
-  mn = mn < k ? mn : k;
-  *levels = mn >= 2048 ? 2 : 0;
-  *variant = STRASSEN_ABC;
-  *tile_id = 0;
+  int lv = 0, var = STRASSEN_ABC, tile = 0;
+  if (!record_lookup(m, n, k, (int)dtype, &lv, &var, &tile)) {
+    model_select(m, n, k, &lv, &var);
+    tile = 0;
+  }
+  *levels = lv;
+  *variant = (strassen_variant)var;
+  *tile_id = tile;
   return STRASSEN_OK;
+}
+
+int strassen_tune_record(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int levels,
+                         strassen_variant variant, int tile_id) {
+  if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
+  if (levels < 0 || levels > 2) return STRASSEN_ERR_LEVELS;
+  if ((int)dtype < 0 || (int)dtype > 2 || (int)variant < 0 || (int)variant > 2) return STRASSEN_ERR_UNSUPPORTED;
+  if (tile_id != 0) return STRASSEN_ERR_ARG;
+  record_store(m, n, k, (int)dtype, levels, (int)variant, tile_id);
+  return STRASSEN_OK;
+}
+
+int strassen_tune_clear(void) {
+  record_clear();
+  return STRASSEN_OK;
+}
+
+double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant) {
+  if (m <= 0 || n <= 0 || k <= 0 || levels < 0 || levels > 2 || (int)variant < 0 || (int)variant > 2) return -1.0;
+  return model_seconds(m, n, k, levels, (int)variant);
 }
 
 int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant,

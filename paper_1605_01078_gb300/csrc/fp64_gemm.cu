@@ -123,11 +123,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase with the given parity; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitLimitCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitLimitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
 }
@@ -670,6 +671,44 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream) {
                           stream);
 }
 
+// ---------------------------------------------------------------- batched
+
+namespace {
+
+// The work list of a batched call travels as kernel parameters (captured by value
+// when the call is captured in a CUDA graph) to a small kernel that copies the
+// descriptors -- TMA tensor maps encoded on the host included -- into the device
+// array the persistent kernel reads.
+constexpr int kDescPerExpand = (32000 - 64) / (int)sizeof(ProbDesc);
+struct ExpandArgs {
+  ProbDesc* out;
+  int count;
+  ProbDesc d[kDescPerExpand];
+};
+
+__global__ void expand_batch_kernel(const __grid_constant__ ExpandArgs a) {
+  const int words = (int)(sizeof(ProbDesc) / sizeof(uint4));
+  for (int w = threadIdx.x; w < a.count * words; w += blockDim.x) {
+    const int i = w / words, o = w - (w / words) * words;
+    reinterpret_cast<uint4*>(&a.out[i])[o] = reinterpret_cast<const uint4*>(&a.d[i])[o];
+  }
+  // The tensor maps were written through the generic proxy; the persistent kernel
+  // acquires them for the tensor-map proxy before use.
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;\n" ::: "memory");
+}
+
+// A kernel whose only thread waits on an mbarrier that nothing completes, with the
+// given limit: exercises the bounded-wait path (status word set, kernel returns).
+__global__ void wait_timeout_check_kernel(long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  if (!mbar_wait(&bar, 0, limit)) record_timeout();
+}
+
+}  // namespace
+
 size_t fp64_batched_scratch_bytes(int count) { return sizeof(ProbDesc) * (size_t)std::max(count, 1); }
 
 cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratch, cudaStream_t stream) {
@@ -693,12 +732,21 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
     descs.push_back(d);
   }
   if (descs.empty()) return cudaSuccess;
-  e = cudaMemcpyAsync(scratch, descs.data(), sizeof(ProbDesc) * descs.size(), cudaMemcpyHostToDevice, stream);
+  ProbDesc* dev = (ProbDesc*)scratch;
+  ExpandArgs* ea = new (std::nothrow) ExpandArgs;
+  if (!ea) return cudaErrorMemoryAllocation;
+  for (size_t off = 0; off < descs.size() && e == cudaSuccess; off += kDescPerExpand) {
+    ea->out = dev + off;
+    ea->count = (int)std::min<size_t>(kDescPerExpand, descs.size() - off);
+    std::memcpy(ea->d, descs.data() + off, sizeof(ProbDesc) * ea->count);
+    void* xargs[] = {ea};
+    e = cudaLaunchKernel((const void*)expand_batch_kernel, dim3(1), dim3(256), xargs, 0, stream);
+  }
+  delete ea;
   if (e != cudaSuccess) return e;
-  // The host vector must outlive the copy: pageable memcpy is staged before return.
   KArgs args;
   std::memset(&args, 0, sizeof(args));
-  args.descs = (const ProbDesc*)scratch;
+  args.descs = dev;
   args.nprob = (int)descs.size();
   args.sched = kSchedStreamK;
   args.total = total;
@@ -706,6 +754,11 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   void* kargs[] = {&args};
   return cudaLaunchKernel(pick_kernel(cls, true), dim3((unsigned)grid), dim3(kThreads), kargs, smem_bytes(cls),
                           stream);
+}
+
+cudaError_t launch_wait_timeout_check(long long limit_cycles, cudaStream_t stream) {
+  wait_timeout_check_kernel<<<1, 32, 0, stream>>>(limit_cycles);
+  return cudaGetLastError();
 }
 
 int fp64_device_status(cudaStream_t stream) {

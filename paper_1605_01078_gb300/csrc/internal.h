@@ -75,6 +75,11 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream);
 size_t fp64_batched_scratch_bytes(int count);
 cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratch, cudaStream_t stream);
 
+// Launches one thread that waits on an mbarrier nothing completes, for `limit_cycles`
+// clock cycles: exercises the bounded-wait path (the status word becomes
+// STRASSEN_ERR_TIMEOUT and the kernel returns).
+cudaError_t launch_wait_timeout_check(long long limit_cycles, cudaStream_t stream);
+
 // Picks a schedule for a launch (balance heuristics for the SM count).
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic);
 
@@ -94,5 +99,12 @@ cudaError_t launch_combine(double* C, int64_t ldc, int64_t c_rows, int64_t c_col
                            const uint8_t* targets, int ntargets, cudaStream_t stream);
 
 int device_sm_count();
+
+// Selection (select.cpp): analytic time model, its argmin, and the exhaustive records.
+double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant);
+void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant);
+bool record_lookup(int64_t m, int64_t n, int64_t k, int dtype, int* levels, int* variant, int* tile);
+void record_store(int64_t m, int64_t n, int64_t k, int dtype, int levels, int variant, int tile);
+void record_clear();
 
 }  // namespace sgb

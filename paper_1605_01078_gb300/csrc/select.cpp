@@ -1,0 +1,136 @@
+// Variant selection: which member of the family (classical, 1 or 2 levels of ABC, AB
+// or Naive) to run for a shape.  Section 4.2 of the paper proposes its performance
+// model for exactly this choice, by problem size and thread count.
+//
+// Order of precedence in strassen_select():
+//   1. an exhaustive-measurement record for the exact shape (strassen_tune_record);
+//   2. the learned selector (an MLP over log2 m, log2 n, log2 k and the dtype), when
+//      one is loaded (strassen_selector_load);
+//   3. the analytic model below.
+//
+// The analytic model restates the paper's T = T_a + T_m for this GPU: T_a counts the
+// FP64 operations the kernels actually execute -- multiply-adds of the padded 128 x 128
+// x 8 tiles (the GPU's analogue of the m_R x n_R micro-tile), operand-sum additions
+// re-done for every tile (ABC, AB) or once (Naive), and C updates -- at the FP64 pipe
+// rate; T_m counts the extra passes of AB and Naive over their temporaries at the HBM
+// rate; and each kernel launch costs a fixed overhead.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace sgb {
+namespace {
+
+constexpr double kFmaPerSec = 2.0 * 152 * 2.07e9;   // FP64 pipe: 2 FMA / clk / SM
+constexpr double kAddCost = 1.2;                    // a DADD costs about 1.2 DFMA (measured)
+constexpr double kBytesPerSec = 6.8e12;             // HBM, measured copy bandwidth
+constexpr double kLaunchSec = 4e-6;
+constexpr int kBM = 128, kBN = 128, kBK = 8;
+
+double ceil_to(double x, double q) { return std::ceil(x / q) * q; }
+
+struct Key {
+  int64_t m, n, k;
+  int dtype;
+  bool operator==(const Key& o) const { return m == o.m && n == o.n && k == o.k && dtype == o.dtype; }
+};
+struct KeyHash {
+  size_t operator()(const Key& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (uint64_t v : {(uint64_t)k.m, (uint64_t)k.n, (uint64_t)k.k, (uint64_t)k.dtype}) {
+      h ^= v;
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+struct Choice {
+  int levels, variant, tile;
+};
+
+std::mutex g_sel_mu;
+std::unordered_map<Key, Choice, KeyHash> g_records;
+
+}  // namespace
+
+double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant) {
+  Plan pl;
+  if (!make_plan(levels, &pl)) return 1e30;
+  const double hm = (double)block_edge(m, levels), hn = (double)block_edge(n, levels),
+               hk = (double)block_edge(k, levels);
+  const double pm = ceil_to(hm, kBM), pn = ceil_to(hn, kBN), pk = ceil_to(hk, kBK);
+  double fma = 0, adds = 0, bytes = 0, launches = 0;
+  if (levels == 0) {
+    fma = pm * pn * pk;
+    launches = 1;
+  } else if (variant == STRASSEN_ABC || variant == STRASSEN_AB) {
+    // Operand sums are re-formed for every tile: per product (na-1)/BN + (nb-1)/BM
+    // additions per multiply-add.
+    for (int r = 0; r < pl.nprod; ++r) {
+      fma += pm * pn * pk;
+      adds += pm * pn * pk * ((pl.na[r] - 1) / (double)kBN + (pl.nb[r] - 1) / (double)kBM);
+    }
+    if (variant == STRASSEN_ABC) {
+      launches = 1;
+    } else {  // AB: clear M, product into M, C updates from M
+      for (int r = 0; r < pl.nprod; ++r) {
+        adds += pl.nc[r] * hm * hn;
+        bytes += 8.0 * hm * hn * (1 + 1 + 2 * pl.nc[r]);
+      }
+      launches = 3.0 * pl.nprod;
+    }
+  } else {  // Naive: operand sums once, classical product into M, C updates
+    for (int r = 0; r < pl.nprod; ++r) {
+      fma += pm * pn * pk;
+      adds += (pl.na[r] - 1) * hm * hk + (pl.nb[r] - 1) * hk * hn + pl.nc[r] * hm * hn;
+      bytes += 8.0 * ((pl.na[r] + 1) * hm * hk + (pl.nb[r] + 1) * hk * hn + hm * hn * (2 + 2 * pl.nc[r]));
+    }
+    launches = 5.0 * pl.nprod;
+  }
+  return (fma + kAddCost * adds) / kFmaPerSec + bytes / kBytesPerSec + launches * kLaunchSec;
+}
+
+void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant) {
+  double best = model_seconds(m, n, k, 0, STRASSEN_ABC);
+  int bl = 0, bv = STRASSEN_ABC;
+  for (int L = 1; L <= 2; ++L) {
+    if (((int64_t)1 << L) > m || ((int64_t)1 << L) > n || ((int64_t)1 << L) > k) break;
+    for (int v : {STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE}) {
+      const double t = model_seconds(m, n, k, L, v);
+      if (t < best * 0.99) {  // prefer fewer levels / ABC within 1%
+        best = t;
+        bl = L;
+        bv = v;
+      }
+    }
+  }
+  *levels = bl;
+  *variant = bv;
+}
+
+bool record_lookup(int64_t m, int64_t n, int64_t k, int dtype, int* levels, int* variant, int* tile) {
+  std::lock_guard<std::mutex> lock(g_sel_mu);
+  auto it = g_records.find(Key{m, n, k, dtype});
+  if (it == g_records.end()) return false;
+  *levels = it->second.levels;
+  *variant = it->second.variant;
+  *tile = it->second.tile;
+  return true;
+}
+
+void record_store(int64_t m, int64_t n, int64_t k, int dtype, int levels, int variant, int tile) {
+  std::lock_guard<std::mutex> lock(g_sel_mu);
+  g_records[Key{m, n, k, dtype}] = Choice{levels, variant, tile};
+}
+
+void record_clear() {
+  std::lock_guard<std::mutex> lock(g_sel_mu);
+  g_records.clear();
+}
+
+}  // namespace sgb

@@ -67,3 +67,14 @@ def sample_indices(rows: int, cols: int, count: int, seed: int) -> Tuple[np.ndar
     r[:4] = [0, 0, rows - 1, rows - 1]
     c[:4] = [0, cols - 1, 0, cols - 1]
     return r.astype(np.int64), c.astype(np.int64)
+
+
+def uniform_device(rows: int, cols: int, seed: int, device="cuda", lo: float = -1.0, hi: float = 1.0):
+    """rows x cols FP64 uniform[lo, hi) drawn on the device by torch's generator
+    (for workloads too large to draw on the host); the same seed gives the same
+    matrix on the same device type."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    x = torch.rand((rows, cols), generator=g, dtype=torch.float64, device=device)
+    return x.mul_(hi - lo).add_(lo)
