@@ -1,0 +1,119 @@
+"""Oracle of the split-precision (Ozaki-style) FP64 product -- TEST INFRASTRUCTURE ONLY.
+
+Not a method of the paper; it follows the error-free splitting of Ozaki, Ogita, Oishi
+and Rump, "Error-free transformations of matrix multiplication by using fast
+routines of matrix multiplication and its applications", Numer. Algorithms 59 (2012),
+with the splitting carried out on integer digits (as in Mukunoki, Ozaki, Ogita and
+Imamura, "DGEMM using tensor cores, and its accurate and reproducible versions",
+ISC 2020).  The scheme computed here, step by step:
+
+1. Scale.  For each row i of X: e_i is the smallest integer with
+   max_k |X_ik| < 2^(e_i - 1)  (e_i = frexp(max)+1; rows of zeros get e_i = 0).
+   For each column j of V: f_j likewise over max_k |V_kj|.  Then
+   u_ik = X_ik * 2^-e_i and w_kj = V_kj * 2^-f_j lie in (-1/2, 1/2).
+2. Split into S balanced base-2^b digits (b = 7): u_0 = u;
+   d_s = rint(2^b * u_{s-1}),  u_s = 2^b * u_{s-1} - d_s  (both exact in FP64),
+   so u = sum_s d_s 2^(-b s) + u_S 2^(-b S) with |d_s| <= 2^(b-1) = 64 and
+   |u_S| <= 1/2.  Every digit is an integer of at most 7 bits: exactly representable in
+   BF16, and a product of two digits is exact in FP32.
+3. Products of slices.  For each weight w = 2 .. S+1, the exact integer matrix
+   G_w = sum_{s + t = w} D_s^X D_t^V  (pairs with s + t > S + 1 are dropped).
+4. Recombine in FP64: acc = G_{S+1} 2^(-b(S+1)); then for w = S down to 2:
+   acc = acc + G_w 2^(-b w)  (each term exact; one rounding per addition);
+   M_ij = acc_ij * 2^(e_i + f_j)  (exact scaling).
+
+For Strassen (Eq. 4) the operand sums sum_s delta_s X_s and sum_t eps_t V_t are formed in
+FP64 first (left to right over the table's terms), split as above, and each product's
+M_r is added into its C blocks, C_q = C_q + gamma_q M_r, in product order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import tables
+
+B_BITS = 7
+
+
+def scale_exponents_rows(X: np.ndarray) -> np.ndarray:
+    """e_i = smallest integer with max_k |X_ik| < 2^(e_i - 1); 0 for a zero row."""
+    mx = np.max(np.abs(X), axis=1) if X.shape[1] else np.zeros(X.shape[0])
+    _, ex = np.frexp(mx)          # mx = f * 2^ex with 0.5 <= f < 1, so mx < 2^ex
+    e = ex.astype(np.int64) + 1   # mx < 2^(e - 1)
+    e[mx == 0] = 0
+    return e
+
+
+def split(U: np.ndarray, S: int, b: int = B_BITS) -> np.ndarray:
+    """Digits of U (entries in (-1/2, 1/2)): array [S, rows, cols] of integers (as
+    float64) with U = sum_s D[s-1] 2^(-b s) + remainder."""
+    out = np.empty((S,) + U.shape)
+    u = np.array(U, dtype=np.float64, copy=True)
+    for s in range(S):
+        t = u * (2.0 ** b)
+        d = np.rint(t)
+        u = t - d
+        out[s] = d
+    return out
+
+
+def slice_product_groups(DX: np.ndarray, DV: np.ndarray) -> dict:
+    """G_w = sum_{s+t=w} DX[s-1] @ DV[t-1] for w = 2..S+1, exact (int64 matmul)."""
+    S = DX.shape[0]
+    X64 = DX.astype(np.int64)
+    V64 = DV.astype(np.int64)
+    G = {}
+    for w in range(2, S + 2):
+        acc = np.zeros((DX.shape[1], DV.shape[2]), dtype=np.int64)
+        for s in range(1, w):
+            t = w - s
+            if t > S:
+                continue
+            acc += X64[s - 1] @ V64[t - 1]
+        G[w] = acc
+    return G
+
+
+def recombine(G: dict, e: np.ndarray, f: np.ndarray, S: int, b: int = B_BITS) -> np.ndarray:
+    acc = np.ldexp(G[S + 1].astype(np.float64), -b * (S + 1))
+    for w in range(S, 1, -1):
+        acc = acc + np.ldexp(G[w].astype(np.float64), -b * w)
+    return np.ldexp(acc, (e[:, None] + f[None, :]).astype(np.int64))
+
+
+def product(X: np.ndarray, V: np.ndarray, S: int = 8) -> np.ndarray:
+    """M ~= X @ V by steps 1-4 (the split-precision product of one pair of operands)."""
+    e = scale_exponents_rows(X)
+    f = scale_exponents_rows(V.T)
+    U = np.ldexp(X, -e[:, None])
+    Wt = np.ldexp(V, -f[None, :])
+    DX = split(U, S)
+    DV = split(Wt, S)
+    return recombine(slice_product_groups(DX, DV), e, f, S)
+
+
+def gemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int, S: int = 8) -> np.ndarray:
+    """C + A @ B with ``levels`` levels of Strassen (table of Eq. 4) and every product
+    M_r computed by the split-precision product; returns a new array."""
+    tab = tables.table(levels)
+    out = np.array(C, dtype=np.float64, copy=True)
+    m, n = C.shape
+    P = 1 << levels
+    hm, hn = -(-m // P), -(-n // P)
+    for (at, bt, ct) in tab:
+        X = None
+        for (i, j, s) in at:
+            blk = tables.block(A, levels, i, j)
+            X = (blk if s > 0 else -blk) if X is None else (X + blk if s > 0 else X - blk)
+        V = None
+        for (i, j, s) in bt:
+            blk = tables.block(B, levels, i, j)
+            V = (blk if s > 0 else -blk) if V is None else (V + blk if s > 0 else V - blk)
+        M = product(X, V, S)
+        for (i, j, s) in ct:
+            r0, c0 = i * hm, j * hn
+            r1, c1 = min(r0 + hm, m), min(c0 + hn, n)
+            if r1 > r0 and c1 > c0:
+                blk = M[:r1 - r0, :c1 - c0]
+                out[r0:r1, c0:c1] = out[r0:r1, c0:c1] + blk if s > 0 else out[r0:r1, c0:c1] - blk
+    return out

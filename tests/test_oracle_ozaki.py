@@ -1,0 +1,114 @@
+"""Pins of the split-precision (Ozaki-style) oracle: exact digit splitting, digit
+bounds, exact integer slice products, exactness on integer and single-binade inputs,
+the FP64-level error on random inputs, and its use under Strassen (no GPU)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ozaki
+import workloads as W
+
+
+def test_split_reconstructs_exactly_and_digits_are_bounded():
+    U = np.ldexp(W.uniform(40, 50, 1), -1) * 0.999  # entries in (-1/2, 1/2)
+    S = 5
+    D = ozaki.split(U, S)
+    assert np.all(np.abs(D) <= 64) and np.all(D == np.rint(D))
+    # rebuild the remainder by the same recurrence and check the identity exactly
+    u = U.copy()
+    for s in range(S):
+        u = u * 128.0 - D[s]
+    rebuilt = sum(D[s] * 2.0 ** (-7 * (s + 1)) for s in range(S))
+    assert np.array_equal(rebuilt + u * 2.0 ** (-7 * S), U)
+
+
+def test_eight_digits_cover_one_binade_exactly():
+    """Entries in +-[1/4, 1/2) have 53-bit mantissas ending at 2^-54: eight 7-bit
+    digits (56 bits) represent them with zero remainder."""
+    g = np.random.Generator(np.random.Philox(5))
+    U = np.copysign(g.uniform(0.25, 0.5, size=(30, 30)), g.uniform(-1, 1, size=(30, 30)))
+    D = ozaki.split(U, 8)
+    assert np.array_equal(sum(D[s] * 2.0 ** (-7 * (s + 1)) for s in range(8)), U)
+
+
+def test_scale_exponents():
+    X = np.array([[0.49, -0.1], [0.5, 0.0], [0.0, 0.0], [-3.0, 1.0]])
+    e = ozaki.scale_exponents_rows(X)
+    assert list(e) == [0, 1, 0, 3]
+    for i in (0, 1, 3):
+        assert np.max(np.abs(X[i])) < 2.0 ** (e[i] - 1) and np.max(np.abs(X[i])) >= 2.0 ** (e[i] - 2)
+
+
+def test_group_products_are_exact_integers():
+    g = np.random.Generator(np.random.Philox(9))
+    DX = g.integers(-64, 65, size=(3, 4, 6)).astype(np.float64)
+    DV = g.integers(-64, 65, size=(3, 6, 5)).astype(np.float64)
+    G = ozaki.slice_product_groups(DX, DV)
+    assert sorted(G) == [2, 3, 4]
+    for w in (2, 3, 4):
+        for i in range(4):
+            for j in range(5):
+                ref = sum(int(DX[s - 1, i, p]) * int(DV[w - s - 1, p, j])
+                          for s in range(1, w) if w - s <= 3 for p in range(6))
+                assert G[w][i, j] == ref
+
+
+@pytest.mark.parametrize("m,n,k", [(8, 9, 10), (33, 17, 65)])
+def test_integer_inputs_give_the_exact_product(m, n, k):
+    A, B = W.integer(m, k, 1, lo=-60, hi=60), W.integer(k, n, 2, lo=-60, hi=60)
+    assert np.array_equal(ozaki.product(A, B), A @ B)
+
+
+def test_float_error_is_at_fp64_level():
+    m, n, k = 24, 20, 300
+    A, B = W.uniform(m, k, 3), W.uniform(k, n, 4)
+    got = ozaki.product(A, B, S=8)
+    rows, cols = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    exact = oracle.gemm_sampled(A, B, None, rows.ravel(), cols.ravel()).reshape(m, n)
+    bound = (k + 1) * 2.0 ** -53 * (np.abs(A) @ np.abs(B))  # the classical FP64 bound
+    assert np.all(np.abs(got - exact) <= bound)
+
+
+def test_fewer_slices_lose_accuracy_monotonically():
+    A, B = W.uniform(16, 64, 5), W.uniform(64, 16, 6)
+    ref = A @ B
+    errs = [np.max(np.abs(ozaki.product(A, B, S=s) - ref)) for s in (2, 4, 6)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] > 1e-6
+
+
+@pytest.mark.parametrize("sigma", [0, 4, 10])
+def test_spread_exponents_error_within_scaled_bound(sigma):
+    """Error bound of the scheme: with S = 8 digits of 7 bits the dropped digit tails
+    and slice pairs contribute at most about k 2^(e_i + f_j) 2^-55, and the S-term FP64
+    recombination about k 2^(e_i + f_j) 2^-52; 2^(e_i + f_j) k 2^-50 covers both."""
+    k = 200
+    A, B = W.scaled(20, k, 7, sigma), W.scaled(k, 18, 8, sigma)
+    got = ozaki.product(A, B)
+    rows, cols = np.meshgrid(np.arange(20), np.arange(18), indexing="ij")
+    exact = oracle.gemm_sampled(A, B, None, rows.ravel(), cols.ravel()).reshape(20, 18)
+    e, f = ozaki.scale_exponents_rows(A), ozaki.scale_exponents_rows(B.T)
+    bound = np.ldexp(np.full((20, 18), k * 2.0 ** -50), (e[:, None] + f[None, :]).astype(np.int64))
+    assert np.all(np.abs(got - exact) <= bound)
+    # and a dropped pair group would break it
+    S = 8
+    DX = ozaki.split(np.ldexp(A, -e[:, None]), S)
+    DV = ozaki.split(np.ldexp(B, -f[None, :]), S)
+    G = ozaki.slice_product_groups(DX, DV)
+    G[3] = np.zeros_like(G[3])
+    broken = ozaki.recombine(G, e, f, S)
+    assert not np.all(np.abs(broken - exact) <= bound)
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_strassen_with_split_products_exact_on_integers(levels):
+    A, B, C = W.integer(21, 19, 1), W.integer(19, 23, 2), W.integer(21, 23, 3)
+    got = ozaki.gemm(A, B, C, levels)
+    assert np.array_equal(got, C + A @ B)
+
+
+def test_identity_and_powers_of_two():
+    X = np.ldexp(np.ones((6, 6)), np.arange(36).reshape(6, 6) % 7 - 3)
+    assert np.array_equal(ozaki.product(np.eye(6), X), X)
+    assert np.array_equal(ozaki.product(X, np.eye(6)), X)
