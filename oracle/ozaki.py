@@ -11,16 +11,19 @@ ISC 2020).  The scheme computed here, step by step:
    max_k |X_ik| < 2^(e_i - 1)  (e_i = frexp(max)+1; rows of zeros get e_i = 0).
    For each column j of V: f_j likewise over max_k |V_kj|.  Then
    u_ik = X_ik * 2^-e_i and w_kj = V_kj * 2^-f_j lie in (-1/2, 1/2).
-2. Split into S balanced base-2^b digits (b = 7): u_0 = u;
-   d_s = rint(2^b * u_{s-1}),  u_s = 2^b * u_{s-1} - d_s  (both exact in FP64),
-   so u = sum_s d_s 2^(-b s) + u_S 2^(-b S) with |d_s| <= 2^(b-1) = 64 and
-   |u_S| <= 1/2.  Every digit is an integer of at most 7 bits: exactly representable in
-   BF16, and a product of two digits is exact in FP32.
+2. Split into S balanced base-2^b digits (b = 7) in the integer domain:
+   N = rint(u * 2^(b S))  (u * 2^(bS) is an exact scaling; rint rounds half to even),
+   so |N| <= 2^(bS-1).  Then, most significant first, with q_s = b (S - s):
+   d_s = floor((N_s + 2^(q_s - 1)) / 2^(q_s)),  N_(s+1) = N_s - d_s 2^(q_s)
+   for s < S, and d_S = N_S.  Hence N = sum_s d_s 2^(b (S - s)) exactly and
+   |d_s| <= 2^(b-1) = 64: every digit is exactly representable in BF16 and a product
+   of two digits is exact in FP32.  u = N 2^(-bS) + r with |r| <= 2^(-bS-1).
 3. Products of slices.  For each weight w = 2 .. S+1, the exact integer matrix
    G_w = sum_{s + t = w} D_s^X D_t^V  (pairs with s + t > S + 1 are dropped).
-4. Recombine in FP64: acc = G_{S+1} 2^(-b(S+1)); then for w = S down to 2:
-   acc = acc + G_w 2^(-b w)  (each term exact; one rounding per addition);
-   M_ij = acc_ij * 2^(e_i + f_j)  (exact scaling).
+4. Recombine with one rounding: the integer T = sum_w G_w 2^(b(S+1-w)) is exact
+   (Python integers here), and M_ij = RN(T_ij) * 2^(e_i + f_j - b(S+1)), where RN is
+   the round-to-nearest-even conversion to FP64 and the power-of-two scaling is exact
+   (results in the normal range).
 
 For Strassen (Eq. 4) the operand sums sum_s delta_s X_s and sum_t eps_t V_t are formed in
 FP64 first (left to right over the table's terms), split as above, and each product's
@@ -46,14 +49,15 @@ def scale_exponents_rows(X: np.ndarray) -> np.ndarray:
 
 def split(U: np.ndarray, S: int, b: int = B_BITS) -> np.ndarray:
     """Digits of U (entries in (-1/2, 1/2)): array [S, rows, cols] of integers (as
-    float64) with U = sum_s D[s-1] 2^(-b s) + remainder."""
-    out = np.empty((S,) + U.shape)
-    u = np.array(U, dtype=np.float64, copy=True)
-    for s in range(S):
-        t = u * (2.0 ** b)
-        d = np.rint(t)
-        u = t - d
-        out[s] = d
+    float64), most significant first, with rint(U 2^(bS)) = sum_s D[s-1] 2^(b(S-s))."""
+    N = np.rint(np.ldexp(np.asarray(U, dtype=np.float64), b * S)).astype(np.int64)
+    out = np.empty((S,) + np.shape(U))
+    for s in range(1, S):
+        q = b * (S - s)
+        d = (N + (np.int64(1) << np.int64(q - 1))) >> np.int64(q)   # floor division by 2^q
+        N = N - (d << np.int64(q))
+        out[s - 1] = d
+    out[S - 1] = N
     return out
 
 
@@ -75,10 +79,15 @@ def slice_product_groups(DX: np.ndarray, DV: np.ndarray) -> dict:
 
 
 def recombine(G: dict, e: np.ndarray, f: np.ndarray, S: int, b: int = B_BITS) -> np.ndarray:
-    acc = np.ldexp(G[S + 1].astype(np.float64), -b * (S + 1))
-    for w in range(S, 1, -1):
-        acc = acc + np.ldexp(G[w].astype(np.float64), -b * w)
-    return np.ldexp(acc, (e[:, None] + f[None, :]).astype(np.int64))
+    rows, cols = G[2].shape
+    T = np.zeros((rows, cols), dtype=object)
+    for w in range(2, S + 2):
+        T = T + G[w].astype(object) * (1 << (b * (S + 1 - w)))
+    out = np.empty((rows, cols))
+    for i in range(rows):
+        for j in range(cols):
+            out[i, j] = float(T[i, j])   # Python int -> float rounds to nearest even
+    return np.ldexp(out, (e[:, None] + f[None, :] - b * (S + 1)).astype(np.int64))
 
 
 def product(X: np.ndarray, V: np.ndarray, S: int = 8) -> np.ndarray:

@@ -12,15 +12,23 @@ import workloads as W
 
 def test_split_reconstructs_exactly_and_digits_are_bounded():
     U = np.ldexp(W.uniform(40, 50, 1), -1) * 0.999  # entries in (-1/2, 1/2)
-    S = 5
-    D = ozaki.split(U, S)
-    assert np.all(np.abs(D) <= 64) and np.all(D == np.rint(D))
-    # rebuild the remainder by the same recurrence and check the identity exactly
-    u = U.copy()
-    for s in range(S):
-        u = u * 128.0 - D[s]
-    rebuilt = sum(D[s] * 2.0 ** (-7 * (s + 1)) for s in range(S))
-    assert np.array_equal(rebuilt + u * 2.0 ** (-7 * S), U)
+    for S in (3, 5, 8):
+        D = ozaki.split(U, S)
+        assert np.all(np.abs(D) <= 64) and np.all(D == np.rint(D))
+        N = sum(D[s].astype(np.int64) << (7 * (S - 1 - s)) for s in range(S))
+        assert np.array_equal(N, np.rint(np.ldexp(U, 7 * S)).astype(np.int64))
+        # the digits carry U to within half a unit of the last digit
+        rebuilt = np.ldexp(N.astype(np.float64), -7 * S)
+        assert np.all(np.abs(rebuilt - U) <= 2.0 ** (-7 * S - 1))
+
+
+def test_split_extreme_digits():
+    # the largest magnitude just below 1/2, a tie at every digit, and a negative tie
+    U = np.array([[0.5 - 2.0 ** -56, 2.0 ** -8 * 0.5, -(2.0 ** -8) * 0.5, 0.0]])
+    D = ozaki.split(U, 8)
+    assert np.all(np.abs(D) <= 64)
+    N = sum(D[s].astype(np.int64) << (7 * (7 - s)) for s in range(8))
+    assert np.array_equal(N, np.rint(np.ldexp(U, 56)).astype(np.int64))
 
 
 def test_eight_digits_cover_one_binade_exactly():
@@ -112,3 +120,20 @@ def test_identity_and_powers_of_two():
     X = np.ldexp(np.ones((6, 6)), np.arange(36).reshape(6, 6) % 7 - 3)
     assert np.array_equal(ozaki.product(np.eye(6), X), X)
     assert np.array_equal(ozaki.product(X, np.eye(6)), X)
+
+
+def test_recombination_is_the_correctly_rounded_exact_sum():
+    """Step 4 against exact rational arithmetic: M = RN(sum_w G_w 2^(-7w) 2^(e+f))."""
+    import fractions
+    A, B = W.uniform(5, 40, 11), W.scaled(40, 4, 12, 3)
+    S = 8
+    e, f = ozaki.scale_exponents_rows(A), ozaki.scale_exponents_rows(B.T)
+    DX = ozaki.split(np.ldexp(A, -e[:, None]), S)
+    DV = ozaki.split(np.ldexp(B, -f[None, :]), S)
+    G = ozaki.slice_product_groups(DX, DV)
+    M = ozaki.recombine(G, e, f, S)
+    for i in range(5):
+        for j in range(4):
+            exact = sum(fractions.Fraction(int(G[w][i, j])) * fractions.Fraction(2) ** (-7 * w) for w in G)
+            exact *= fractions.Fraction(2) ** int(e[i] + f[j])
+            assert M[i, j] == float(exact)
