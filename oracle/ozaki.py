@@ -20,8 +20,8 @@ ISC 2020).  The scheme computed here, step by step:
    of two digits is exact in FP32.  u = N 2^(-bS) + r with |r| <= 2^(-bS-1).
 3. Products of slices.  For each weight w = 2 .. S+1, the exact integer matrix
    G_w = sum_{s + t = w} D_s^X D_t^V  (pairs with s + t > S + 1 are dropped).
-4. Recombine with one rounding: the integer T = sum_w G_w 2^(b(S+1-w)) is exact
-   (Python integers here), and M_ij = RN(T_ij) * 2^(e_i + f_j - b(S+1)), where RN is
+4. Recombine with one rounding: the integer T = sum_w G_w 2^(b(S+1-w)) is exact,
+   and M_ij = RN(T_ij) * 2^(e_i + f_j - b(S+1)), where RN is
    the round-to-nearest-even conversion to FP64 and the power-of-two scaling is exact
    (results in the normal range).
 
@@ -79,15 +79,24 @@ def slice_product_groups(DX: np.ndarray, DV: np.ndarray) -> dict:
 
 
 def recombine(G: dict, e: np.ndarray, f: np.ndarray, S: int, b: int = B_BITS) -> np.ndarray:
-    rows, cols = G[2].shape
-    T = np.zeros((rows, cols), dtype=object)
+    """M = RN(T) 2^(e_i + f_j - b(S+1)) with T = sum_w G_w 2^(b(S+1-w)).
+
+    T is carried as two integers, T_hi (weights w <= (S+2)//2) and T_lo (the rest),
+    T = T_hi 2^(b(S+1-W)) + T_lo with W = (S+2)//2.  For the sizes this oracle serves
+    (|G_w| < 2^29) both are below 2^53 in magnitude, so each converts to FP64 exactly,
+    the power-of-two scaling of T_hi is exact, and the one FP64 addition of the two
+    returns the correctly rounded RN(T)."""
+    W = (S + 2) // 2
+    t_hi = np.zeros(G[2].shape, dtype=np.int64)
+    t_lo = np.zeros(G[2].shape, dtype=np.int64)
     for w in range(2, S + 2):
-        T = T + G[w].astype(object) * (1 << (b * (S + 1 - w)))
-    out = np.empty((rows, cols))
-    for i in range(rows):
-        for j in range(cols):
-            out[i, j] = float(T[i, j])   # Python int -> float rounds to nearest even
-    return np.ldexp(out, (e[:, None] + f[None, :] - b * (S + 1)).astype(np.int64))
+        if w <= W:
+            t_hi = t_hi + G[w] * (np.int64(1) << np.int64(b * (W - w)))
+        else:
+            t_lo = t_lo + G[w] * (np.int64(1) << np.int64(b * (S + 1 - w)))
+    assert np.all(np.abs(t_hi) < 2 ** 53) and np.all(np.abs(t_lo) < 2 ** 53)
+    T = np.ldexp(t_hi.astype(np.float64), b * (S + 1 - W)) + t_lo.astype(np.float64)
+    return np.ldexp(T, (e[:, None] + f[None, :] - b * (S + 1)).astype(np.int64))
 
 
 def product(X: np.ndarray, V: np.ndarray, S: int = 8) -> np.ndarray:

@@ -138,6 +138,18 @@ int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, con
   return STRASSEN_OK;
 }
 
+int run_oz(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+           double* C, int64_t ldc, int levels, cudaStream_t s) {
+  Workspace ws;
+  ws.s = s;
+  if (cudaMallocAsync(&ws.p, (size_t)ozaki_workspace_bytes(m, n, k, levels), s) != cudaSuccess) {
+    cudaGetLastError();
+    ws.p = nullptr;
+    return STRASSEN_ERR_ALLOC;
+  }
+  return cuda_status(run_ozaki(m, n, k, A, lda, B, ldb, C, ldc, levels, ws.p, s));
+}
+
 }  // namespace
 
 extern "C" {
@@ -152,7 +164,7 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
     const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
     if (chk < 0) return chk;
     if (chk == 1) return STRASSEN_OK;
-    if (dtype != STRASSEN_F64) return STRASSEN_ERR_UNSUPPORTED;
+    if (dtype == STRASSEN_F64_OZ_INT8) return STRASSEN_ERR_UNSUPPORTED;
     if (levels == -1 || variant == STRASSEN_AUTO) {
       int sl = 0, tile = 0;
       strassen_variant sv = STRASSEN_ABC;
@@ -167,6 +179,7 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
       cudaGetLastError();
       return STRASSEN_ERR_CUDA;
     }
+    if (dtype == STRASSEN_F64_OZ_BF16) return run_oz(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
     if (levels == 0) return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, s);
     switch (variant) {
       case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
@@ -248,7 +261,11 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
   }
 }
 
-int strassen_device_status(strassen_stream_t stream) { return fp64_device_status((cudaStream_t)stream); }
+int strassen_device_status(strassen_stream_t stream) {
+  const int a = fp64_device_status((cudaStream_t)stream);
+  const int b = ozaki_device_status();
+  return a != STRASSEN_OK ? a : b;
+}
 
 int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stream_t stream) {
   if (limit_cycles < 0) return STRASSEN_ERR_ARG;
@@ -262,7 +279,12 @@ int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* 
   if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
   int lv = 0, var = STRASSEN_ABC, tile = 0;
   if (!record_lookup(m, n, k, (int)dtype, &lv, &var, &tile)) {
-    model_select(m, n, k, &lv, &var);
+    if (dtype == STRASSEN_F64) {
+      model_select(m, n, k, &lv, &var);
+    } else {  // split precision: tensor-core products, no FP64 model; classical slices
+      lv = 0;
+      var = STRASSEN_ABC;
+    }
     tile = 0;
   }
   *levels = lv;
@@ -306,6 +328,8 @@ int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, str
     if (variant == STRASSEN_AUTO) variant = sv;
   }
   levels = clamp_levels(levels, m, n, k);
+  if (dtype == STRASSEN_F64_OZ_INT8) return STRASSEN_ERR_UNSUPPORTED;
+  if (dtype == STRASSEN_F64_OZ_BF16) return ozaki_workspace_bytes(m, n, k, levels);
   if (levels == 0 || variant == STRASSEN_ABC) return 0;
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
   if (variant == STRASSEN_AB) return (int64_t)sizeof(double) * hm * hn;

@@ -100,6 +100,14 @@ cudaError_t launch_combine(double* C, int64_t ldc, int64_t c_rows, int64_t c_col
 
 int device_sm_count();
 
+// Split-precision products (ozaki.cu): workspace bytes, the launch sequence (split,
+// tensor-core slice products, recombine + scatter) on caller-provided workspace, and
+// the read-and-clear of its device status word.
+int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels);
+cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream);
+int ozaki_device_status();
+
 // Selection (select.cpp): analytic time model, its argmin, and the exhaustive records.
 double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant);
 void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant);

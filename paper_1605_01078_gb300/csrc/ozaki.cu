@@ -1,0 +1,721 @@
+// Split-precision FP64 products on the tensor cores (dtype STRASSEN_F64_OZ_BF16).
+//
+// Each Strassen product M_r = (sum_s delta_s X_s)(sum_t eps_t V_t) of Eq. 4 is
+// computed from integer slices of its two FP64 operands (the error-free splitting of
+// Ozaki, Ogita, Oishi and Rump, carried out on integer digits):
+//
+//   1. split (oz_split_rows / oz_split_cols): form the operand sum in FP64; scale each
+//      row of X^ (column of V^) by 2^-e so that it lies in (-1/2, 1/2), with e the
+//      smallest integer such that the row maximum is below 2^(e-1); round to the
+//      integer N = rint(x 2^(56 - e)) -- an exact scaling followed by round-to-nearest-
+//      even, done here with integer operations on the bits of x -- and cut N into
+//      S = 8 balanced base-128 digits (most significant first, d = floor((N + 2^(q-1))
+//      / 2^q)), |d| <= 64: exact in BF16;
+//   2. slice products (oz_gemm, tcgen05 + TMEM): for every weight w = s + t <= 9 the
+//      exact integer G_w = sum_{s+t=w} D_s^X D_t^V.  BF16 x BF16 products of digits are
+//      exact in FP32 and every FP32 accumulation chunk holds at most 1024 of them
+//      (|sum| < 2^22), so the tensor-core accumulator stays exact; the epilogue warps
+//      convert each chunk to an integer and fold the groups into two int64 Horner
+//      sums, T_hi = sum_{w<=5} G_w 2^(7(5-w)) and T_lo = sum_{w>=6} G_w 2^(7(9-w));
+//   3. recombine + scatter (oz_recombine_scatter): T = T_hi 2^28 + T_lo exactly in
+//      128-bit integers, M = RN(T) 2^(e_i + f_j - 63) with a single round-to-nearest-even
+//      conversion (integer operations), and C_q = C_q + gamma_q M_r for every product in
+//      table order (the ABC scatter, one owner thread per C element).
+//
+// GB300 notes.  FP64 arithmetic runs at about 2 lanes per clock per SM here, so the
+// split and recombine steps use integer arithmetic for everything but the operand sums
+// and the final C additions; the products run on the BF16 tensor cores (tcgen05.mma
+// kind::f16, 128x128 tiles, accumulators in tensor memory) fed by TMA with 128-byte
+// swizzle.  INT8 slices are not used: the INT8 tensor rate of this part (measured
+// 150 TOP/s) is far below its BF16 rate (1950 TFLOP/s).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace sgb {
+namespace {
+
+__constant__ PlanTables c_oz_plans = kPlanTables;
+__device__ int g_oz_status;
+
+constexpr int kS = 8;          // digits per operand
+constexpr int kB = 7;          // bits per digit
+constexpr int kWSplit = 5;     // groups 2..5 -> T_hi, 6..9 -> T_lo
+constexpr int kTM = 128, kTN = 128, kTK = 64;  // tile; kTK bf16 = one 128-byte row
+constexpr int kStages = 6;
+constexpr int kChunkItems = 16;  // k-blocks of 64 per exact FP32 chunk (1024 products)
+constexpr int kThreads = 384;    // warp 0 TMA, warp 1 MMA + TMEM, warps 4..11 epilogue
+constexpr int kEpiThreads = 256;
+constexpr long long kWaitLimit = 2000000000LL;
+constexpr int kLaunchRegs = 168, kLowRegs = 40, kHighRegs = 232;
+static_assert(128 * kLowRegs + 256 * kHighRegs == kThreads * kLaunchRegs, "register split");
+
+// ---------------------------------------------------------------- integer helpers
+
+// Smallest e with |x| < 2^(e-1) for the magnitude bits `mag` of a finite double
+// (0 for zero).
+__device__ __forceinline__ int scale_exponent(unsigned long long mag) {
+  if (mag == 0) return 0;
+  const int E = (int)(mag >> 52);
+  if (E > 0) return E - 1021;
+  return (64 - __clzll((long long)mag)) - 1073;  // subnormal
+}
+
+// rint(x * 2^(56 - e)) as an integer, computed on the bits of x (|x| < 2^(e-1)).
+__device__ __forceinline__ long long scaled_rint(double x, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = bits & 0x7fffffffffffffffULL;
+  if (mag == 0) return 0;
+  int E = (int)(mag >> 52);
+  unsigned long long M = mag & ((1ULL << 52) - 1);
+  if (E == 0) E = 1; else M |= (1ULL << 52);
+  // x = M 2^(E - 1075), so x 2^(56 - e) = M 2^(E - 1019 - e)
+  const int sh = E - 1019 - e;
+  unsigned long long q;
+  if (sh >= 0) {
+    q = sh < 64 ? (M << sh) : 0;
+  } else {
+    const int r = -sh;
+    if (r >= 63) {
+      q = 0;
+    } else {
+      q = M >> r;
+      const unsigned long long rem = M & ((1ULL << r) - 1), half = 1ULL << (r - 1);
+      if (rem > half || (rem == half && (q & 1ULL))) q += 1;
+    }
+  }
+  return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
+// The S digits of N, most significant first: d = floor((N + 2^(q-1)) / 2^q).
+__device__ __forceinline__ void digits_of(long long N, float* d) {
+#pragma unroll
+  for (int s = 1; s < kS; ++s) {
+    const int q = kB * (kS - s);
+    const long long v = (N + (1LL << (q - 1))) >> q;
+    N -= v * (1LL << q);
+    d[s - 1] = (float)v;
+  }
+  d[kS - 1] = (float)N;
+}
+
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+
+// Operand sum x = sum_t sign_t * src[block_t](r, c), masked to the source extent.
+__device__ __forceinline__ double operand_sum(const double* src, int64_t ld, int64_t rows, int64_t cols,
+                                              int64_t h_r, int64_t h_c, const uint8_t* terms, int nterms,
+                                              int64_t r, int64_t c) {
+  double v = 0.0;
+  for (int t = 0; t < nterms; ++t) {
+    const uint8_t code = terms[t];
+    const int64_t gr = (int64_t)term_bi(code) * h_r + r, gc = (int64_t)term_bj(code) * h_c + c;
+    double x = 0.0;
+    if (r < h_r && c < h_c && gr < rows && gc < cols) x = src[gr * ld + gc];
+    if (t == 0) v = term_neg(code) ? -x : x;
+    else v = term_neg(code) ? v - x : v + x;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- split kernels
+
+struct SplitArgs {
+  const double* src;
+  int64_t ld, rows, cols;   // source matrix (A: m x k, B: k x n)
+  int64_t h_r, h_c;         // block edges along the source's rows and columns
+  int64_t h_out, h_outp;    // output rows (h_m or h_n) and padded rows
+  int64_t h_k, h_kp;        // reduction length and padded length
+  int plan_off;             // table row of product 0
+  __nv_bfloat16* slices;    // [P][S][h_outp][h_kp]
+  int* exps;                // [P][h_outp]
+};
+
+// One block per output row i of X^ (rows of A's operand sum), product blockIdx.y.
+__global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
+  extern __shared__ double rowbuf[];  // h_k doubles
+  __shared__ unsigned long long red[32];
+  const int p = blockIdx.y;
+  const int64_t i = blockIdx.x;
+  const int row = a.plan_off + p;
+  const int nt = c_oz_plans.na[row];
+  uint8_t terms[kMaxTerms];
+  for (int t = 0; t < kMaxTerms; ++t) terms[t] = c_oz_plans.ta[row][t];
+  __nv_bfloat16* out = a.slices + ((int64_t)p * kS * a.h_outp + i) * a.h_kp;
+  const int64_t slice_stride = a.h_outp * a.h_kp;
+  if (i >= a.h_out) {  // padding rows
+    for (int64_t k = threadIdx.x; k < a.h_kp; k += blockDim.x)
+      for (int s = 0; s < kS; ++s) out[s * slice_stride + k] = __float2bfloat16(0.0f);
+    if (threadIdx.x == 0) a.exps[(int64_t)p * a.h_outp + i] = 0;
+    return;
+  }
+  unsigned long long mx = 0;
+  for (int64_t k = threadIdx.x; k < a.h_k; k += blockDim.x) {
+    const double x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, i, k);
+    rowbuf[k] = x;
+    mx = max(mx, mag_bits(x));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) red[0] = v;
+  }
+  __syncthreads();
+  const int e = scale_exponent(red[0]);
+  if (threadIdx.x == 0) a.exps[(int64_t)p * a.h_outp + i] = e;
+  for (int64_t k = threadIdx.x; k < a.h_kp; k += blockDim.x) {
+    float d[kS];
+    digits_of(k < a.h_k ? scaled_rint(rowbuf[k], e) : 0, d);
+#pragma unroll
+    for (int s = 0; s < kS; ++s) out[s * slice_stride + k] = __float2bfloat16(d[s]);
+  }
+}
+
+// One block per 64 output columns j of V^ (columns of B's operand sum), product
+// blockIdx.y.  The slices are written transposed ([j][k], k contiguous) through a
+// shared-memory tile.
+constexpr int kColTilePitch = 64 + 8;  // bf16 per tile row (padding against bank conflicts)
+constexpr size_t kSplitColsSmem = sizeof(__nv_bfloat16) * kS * 64 * kColTilePitch;
+
+__global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ SplitArgs a) {
+  __shared__ unsigned long long colmax[4][64];
+  extern __shared__ __align__(16) __nv_bfloat16 tile_raw[];  // [kS][64][kColTilePitch]
+  auto tile = [&](int s, int c, int k) -> __nv_bfloat16& { return tile_raw[(s * 64 + c) * kColTilePitch + k]; };
+  const int p = blockIdx.y;
+  const int64_t j0 = (int64_t)blockIdx.x * 64;
+  const int row = a.plan_off + p;
+  const int nt = c_oz_plans.nb[row];
+  uint8_t terms[kMaxTerms];
+  for (int t = 0; t < kMaxTerms; ++t) terms[t] = c_oz_plans.tb[row][t];
+  const int tid = threadIdx.x, c = tid & 63, ph = tid >> 6;
+  // Column maxima over the reduction dimension (rows of B's operand sum).
+  unsigned long long mx = 0;
+  if (j0 + c < a.h_out)
+    for (int64_t k = ph; k < a.h_k; k += 4)
+      mx = max(mx, mag_bits(operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j0 + c)));
+  colmax[ph][c] = mx;
+  __syncthreads();
+  if (tid < 64) {
+    const unsigned long long v = max(max(colmax[0][tid], colmax[1][tid]), max(colmax[2][tid], colmax[3][tid]));
+    colmax[0][tid] = v;
+    if (j0 + tid < a.h_outp) a.exps[(int64_t)p * a.h_outp + j0 + tid] = (j0 + tid < a.h_out) ? scale_exponent(v) : 0;
+  }
+  __syncthreads();
+  const int64_t slice_stride = a.h_outp * a.h_kp;
+  __nv_bfloat16* out = a.slices + (int64_t)p * kS * slice_stride;
+  for (int64_t k0 = 0; k0 < a.h_kp; k0 += 64) {
+    for (int q = 0; q < 16; ++q) {
+      const int e = tid + 256 * q;
+      const int kk = e >> 6, cc = e & 63;
+      const int64_t k = k0 + kk, j = j0 + cc;
+      float d[kS];
+      long long N = 0;
+      if (j < a.h_out && k < a.h_k) {
+        const double x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j);
+        N = scaled_rint(x, scale_exponent(colmax[0][cc]));
+      }
+      digits_of(N, d);
+#pragma unroll
+      for (int s = 0; s < kS; ++s) tile(s, cc, kk) = __float2bfloat16(d[s]);
+    }
+    __syncthreads();
+    // 64 columns x 64 k per digit; each thread writes 16 consecutive k of one column.
+    const int cc = tid >> 2, part = tid & 3;
+    if (j0 + cc < a.h_outp) {
+      for (int s = 0; s < kS; ++s) {
+        __nv_bfloat16* dst = out + s * slice_stride + (j0 + cc) * a.h_kp + k0 + part * 16;
+        const uint4* srcv = reinterpret_cast<const uint4*>(&tile(s, cc, part * 16));
+        uint4* dstv = reinterpret_cast<uint4*>(dst);
+        dstv[0] = srcv[0];
+        dstv[1] = srcv[1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- tcgen05 helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > kWaitLimit) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand tile with 128-byte swizzle, rows of
+// 128 bytes, 8-row swizzle atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M = N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// ---------------------------------------------------------------- slice-product kernel
+
+struct GemmArgs {
+  CUtensorMap tmA;  // DX of all products as rows [P*S*h_mp] x cols [h_kp], bf16
+  CUtensorMap tmB;  // DV of all products as rows [P*S*h_np] x cols [h_kp]
+  long long* t_hi;  // [P][h_mp][h_np]
+  long long* t_lo;
+  int P, tiles_m, tiles_n, nkb;
+  int64_t h_mp, h_np;
+};
+
+// Number of (pair, k-block) items of group w: pairs s + t = w with 1 <= s, t <= S.
+__host__ __device__ constexpr int pairs_of(int w) {
+  return (w - 1 < kS ? w - 1 : kS) - (w - kS > 1 ? w - kS : 1) + 1;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ GemmArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm_raw[];
+  // 1024-byte aligned stage ring for the 128-byte swizzle
+  uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* stA = sm;                               // [kStages][128][128 B]
+  uint8_t* stB = sm + kStages * kTM * 128;         // [kStages][128][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stB + kStages * kTN * 128);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* tfull = bars + 2 * kStages;
+  uint64_t* tempty = bars + 2 * kStages + 2;
+  uint64_t* drain = bars + 2 * kStages + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], kEpiThreads); }
+    mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(smem_u32(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    tc_fence_before();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int tiles = a.tiles_m * a.tiles_n;
+  const int units = a.P * tiles;
+  int group_items[kS + 2];
+#pragma unroll
+  for (int w = 2; w <= kS + 1; ++w) group_items[w] = pairs_of(w) * a.nkb;
+
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kLowRegs));
+    if (warp == 0 && lane == 0) {
+      // ------------------------------------------------ TMA producer
+      uint32_t it = 0;
+      bool bad = false;
+      for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+        const int p = u / tiles, t = u - (u / tiles) * tiles;
+        const int tm = t / a.tiles_n, tn = t - (t / a.tiles_n) * a.tiles_n;
+        for (int w = 2; w <= kS + 1 && !bad; ++w) {
+          const int s_lo = w - kS > 1 ? w - kS : 1, s_hi = w - 1 < kS ? w - 1 : kS;
+          for (int s = s_lo; s <= s_hi && !bad; ++s) {
+            const int tt = w - s;
+            const int ya = (int)(((int64_t)p * kS + (s - 1)) * a.h_mp + (int64_t)tm * kTM);
+            const int yb = (int)(((int64_t)p * kS + (tt - 1)) * a.h_np + (int64_t)tn * kTN);
+            for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+              const int st = it % kStages;
+              const uint32_t use = it / kStages;
+              if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) { bad = true; break; }
+              mbar_expect_tx(&full[st], (kTM + kTN) * 128);
+              tma_2d(stA + st * kTM * 128, &a.tmA, kb * kTK, ya, &full[st]);
+              tma_2d(stB + st * kTN * 128, &a.tmB, kb * kTK, yb, &full[st]);
+            }
+          }
+        }
+      }
+      if (bad) {
+        atomicExch(&g_oz_status, STRASSEN_ERR_TIMEOUT);
+        const long long t0 = clock64();  // let copies in flight land before leaving
+        while (clock64() - t0 < 2000000) {}
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      uint32_t it = 0, ch = 0;
+      bool bad = false;
+      for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+        for (int w = 2; w <= kS + 1 && !bad; ++w) {
+          const int n_items = group_items[w];
+          for (int c0 = 0; c0 < n_items && !bad; c0 += kChunkItems, ++ch) {
+            const int buf = ch & 1;
+            const uint32_t use = ch >> 1;
+            if (use > 0 && !mbar_wait(&tempty[buf], (use - 1) & 1)) { bad = true; break; }
+            tc_fence_after();
+            const int c1 = c0 + kChunkItems < n_items ? c0 + kChunkItems : n_items;
+            for (int i = c0; i < c1; ++i, ++it) {
+              const int st = it % kStages;
+              if (!mbar_wait(&full[st], (it / kStages) & 1)) { bad = true; break; }
+              tc_fence_after();
+              const uint64_t ad = sw128_desc(smem_u32(stA + st * kTM * 128));
+              const uint64_t bd = sw128_desc(smem_u32(stB + st * kTN * 128));
+#pragma unroll
+              for (int k = 0; k < kTK / 16; ++k)
+                umma(tmem + buf * kTN, ad + 2 * k, bd + 2 * k, (i > c0 || k > 0) ? 1u : 0u);
+              umma_commit(&empty[st]);
+            }
+            umma_commit(&tfull[buf]);
+          }
+        }
+      }
+      // Wait (bounded) until every issued MMA has completed before TMEM is released.
+      umma_commit(drain);
+      mbar_wait(drain, 0);
+      if (bad) {
+        atomicExch(&g_oz_status, STRASSEN_ERR_TIMEOUT);
+      }
+    }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kHighRegs));
+    // ------------------------------------------------ epilogue warps
+    const int ew = warp - 4;
+    const int g = warp & 3;         // TMEM lane quarter this warp may read
+    const int half = ew >> 2;       // column half of the tile
+    uint32_t ch = 0;
+    bool bad = false;
+    long long R[64];
+    for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+      const int p = u / tiles, t = u - (u / tiles) * tiles;
+      const int tm = t / a.tiles_n, tn = t - (t / a.tiles_n) * a.tiles_n;
+#pragma unroll
+      for (int q = 0; q < 64; ++q) R[q] = 0;
+      const int64_t row = (int64_t)tm * kTM + 32 * g + lane;
+      const int64_t col0 = (int64_t)tn * kTN + 64 * half;
+      for (int w = 2; w <= kS + 1 && !bad; ++w) {
+        if (w != 2 && w != kWSplit + 1) {
+#pragma unroll
+          for (int q = 0; q < 64; ++q) R[q] *= (1LL << kB);
+        }
+        const int n_items = group_items[w];
+        for (int c0 = 0; c0 < n_items; c0 += kChunkItems, ++ch) {
+          const int buf = ch & 1;
+          if (!mbar_wait(&tfull[buf], (ch >> 1) & 1)) { bad = true; break; }
+          tc_fence_after();
+          const uint32_t base = tmem + ((uint32_t)(32 * g) << 16) + buf * kTN + 64 * half;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            uint32_t v[16];
+            tmem_ld16(base + 16 * q, v);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 16; ++i) R[16 * q + i] += (long long)__float2int_rn(__uint_as_float(v[i]));
+          }
+          tc_fence_before();
+          mbar_arrive(&tempty[buf]);
+        }
+        if (bad) break;
+        if (w == kWSplit || w == kS + 1) {
+          long long* dst = (w == kWSplit ? a.t_hi : a.t_lo) + ((int64_t)p * a.h_mp + row) * a.h_np + col0;
+          longlong2* d2 = reinterpret_cast<longlong2*>(dst);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) d2[q] = make_longlong2(R[2 * q], R[2 * q + 1]);
+#pragma unroll
+          for (int q = 0; q < 64; ++q) R[q] = 0;
+        }
+      }
+    }
+    if (bad) {
+      atomicExch(&g_oz_status, STRASSEN_ERR_TIMEOUT);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- recombine + scatter
+
+struct RecombineArgs {
+  double* C;
+  int64_t ldc, m, n;
+  int64_t hm, hn, h_mp, h_np;
+  int levels, P;
+  const long long* t_hi;
+  const long long* t_lo;
+  const int* e;   // [P][h_mp]
+  const int* f;   // [P][h_np]
+};
+
+// RN(T) * 2^scale for T = hi * 2^28 + lo, with integer operations (one rounding).
+__device__ double round_scaled(long long hi, long long lo, int scale) {
+  // 128-bit two's complement T = (th, tl)
+  unsigned long long tl = (unsigned long long)hi << 28;
+  long long th = hi >> 36;
+  const unsigned long long l2 = (unsigned long long)lo;
+  const unsigned long long sum = tl + l2;
+  th += (lo >> 63) + (sum < tl ? 1 : 0);
+  tl = sum;
+  if (th == 0 && tl == 0) return 0.0;
+  const bool neg = th < 0;
+  unsigned long long mh = (unsigned long long)th, ml = tl;
+  if (neg) {  // magnitude
+    ml = ~ml + 1;
+    mh = ~mh + (ml == 0 ? 1 : 0);
+  }
+  const int nb = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
+  unsigned long long mant;
+  int sh = 0;
+  if (nb <= 53) {
+    mant = ml;
+  } else {
+    sh = nb - 53;
+    // mant = M >> sh, rem = M mod 2^sh
+    unsigned long long rem_hi, rem_lo;
+    if (sh >= 64) {
+      mant = mh >> (sh - 64);
+      rem_hi = (sh - 64) ? (mh & ((1ULL << (sh - 64)) - 1)) : 0;
+      rem_lo = ml;
+    } else {
+      mant = (ml >> sh) | (sh ? (mh << (64 - sh)) : 0);
+      rem_hi = 0;
+      rem_lo = ml & ((1ULL << sh) - 1);
+    }
+    // compare rem with half = 2^(sh-1)
+    int cmp;
+    if (sh - 1 >= 64) {
+      const unsigned long long hh = 1ULL << (sh - 1 - 64);
+      cmp = rem_hi > hh ? 1 : (rem_hi < hh ? -1 : (rem_lo > 0 ? 1 : 0));
+    } else {
+      const unsigned long long hl = 1ULL << (sh - 1);
+      cmp = rem_hi > 0 ? 1 : (rem_lo > hl ? 1 : (rem_lo < hl ? -1 : 0));
+    }
+    if (cmp > 0 || (cmp == 0 && (mant & 1ULL))) {
+      mant += 1;
+      if (mant == (1ULL << 53)) { mant >>= 1; sh += 1; }
+    }
+  }
+  // value = mant * 2^(sh + scale), mant < 2^53
+  const int mb = 64 - __clzll((long long)mant);     // bits of mant
+  const int E = (mb - 1) + sh + scale + 1023;       // biased exponent of the result
+  if (E >= 1 && E <= 2046) {
+    const unsigned long long frac = (mant << (53 - mb)) & ((1ULL << 52) - 1);
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)E << 52) | frac));
+  }
+  const double v = scalbn((double)mant, sh + scale);  // outside the normal range
+  return neg ? -v : v;
+}
+
+__global__ void oz_recombine_scatter(const __grid_constant__ RecombineArgs a) {
+  const int Pn = 1 << a.levels;
+  const int64_t per_block = a.hm * a.hn;
+  const int64_t total = per_block * Pn * Pn;
+  const int off = a.levels == 0 ? 0 : (a.levels == 1 ? 1 : 8);  // first table row of the level
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / per_block);
+    const int64_t rem = idx - (int64_t)q * per_block;
+    const int64_t i = rem / a.hn, j = rem - (rem / a.hn) * a.hn;
+    const int qi = q / Pn, qj = q - (q / Pn) * Pn;
+    const int64_t gr = (int64_t)qi * a.hm + i, gc = (int64_t)qj * a.hn + j;
+    if (gr >= a.m || gc >= a.n) continue;
+    double c = a.C[gr * a.ldc + gc];
+    for (int r = 0; r < a.P; ++r) {
+      const int row = off + r;
+      const int nc = c_oz_plans.nc[row];
+      for (int t = 0; t < nc; ++t) {
+        const uint8_t code = c_oz_plans.tc[row][t];
+        if (term_bi(code) != qi || term_bj(code) != qj) continue;
+        const int64_t o = ((int64_t)r * a.h_mp + i) * a.h_np + j;
+        const double M = round_scaled(a.t_hi[o], a.t_lo[o],
+                                      a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
+        c = term_neg(code) ? c - M : c + M;
+      }
+    }
+    a.C[gr * a.ldc + gc] = c;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_oz_encode = nullptr;
+std::once_flag g_oz_once;
+cudaError_t g_oz_init = cudaSuccess;
+size_t oz_gemm_smem() { return (size_t)kStages * (kTM + kTN) * 128 + 1024 + 256; }
+
+void oz_init() {
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    g_oz_init = cudaErrorNotSupported;
+    return;
+  }
+  g_oz_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  g_oz_init = cudaFuncSetAttribute((const void*)oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)oz_gemm_smem());
+  if (g_oz_init == cudaSuccess)
+    g_oz_init = cudaFuncSetAttribute((const void*)oz_split_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSplitColsSmem);
+}
+
+bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols) {
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(cols * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  cuuint32_t estr[2] = {1, 1};
+  return g_oz_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
+
+}  // namespace
+
+int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
+  const int64_t P = kPlanCount[levels];
+  const int64_t hmp = round_up(block_edge(m, levels), kTM), hnp = round_up(block_edge(n, levels), kTN),
+                hkp = round_up(block_edge(k, levels), kTK);
+  return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + 2 * P * hmp * hnp * 8 + 4096;
+}
+
+int ozaki_device_status() {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_oz_status, sizeof(int)) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  if (v != 0) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(g_oz_status, &zero, sizeof(int)) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  }
+  return v;
+}
+
+cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream) {
+  std::call_once(g_oz_once, oz_init);
+  if (g_oz_init != cudaSuccess) return g_oz_init;
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 1;
+  const int P = kPlanCount[levels];
+  const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
+  const int64_t hmp = round_up(hm, kTM), hnp = round_up(hn, kTN), hkp = round_up(hk, kTK);
+  uint8_t* w = (uint8_t*)ws;
+  __nv_bfloat16* DX = (__nv_bfloat16*)w;                       w += (size_t)P * kS * hmp * hkp * 2;
+  __nv_bfloat16* DV = (__nv_bfloat16*)w;                       w += (size_t)P * kS * hnp * hkp * 2;
+  int* ex = (int*)w;                                           w += (size_t)P * hmp * 4;
+  int* fx = (int*)w;                                           w += (size_t)P * hnp * 4;
+  w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+  long long* thi = (long long*)w;                              w += (size_t)P * hmp * hnp * 8;
+  long long* tlo = (long long*)w;
+
+  SplitArgs sa;
+  sa.src = A; sa.ld = lda; sa.rows = m; sa.cols = k; sa.h_r = hm; sa.h_c = hk;
+  sa.h_out = hm; sa.h_outp = hmp; sa.h_k = hk; sa.h_kp = hkp;
+  sa.plan_off = kPlanOffset[levels]; sa.slices = DX; sa.exps = ex;
+  const size_t row_smem = (size_t)hk * sizeof(double);
+  if (row_smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)oz_split_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)row_smem);
+    if (e != cudaSuccess) return e;
+  }
+  oz_split_rows<<<dim3((unsigned)hmp, (unsigned)P), 256, row_smem, stream>>>(sa);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  SplitArgs sb;
+  sb.src = B; sb.ld = ldb; sb.rows = k; sb.cols = n; sb.h_r = hk; sb.h_c = hn;
+  sb.h_out = hn; sb.h_outp = hnp; sb.h_k = hk; sb.h_kp = hkp;
+  sb.plan_off = kPlanOffset[levels]; sb.slices = DV; sb.exps = fx;
+  oz_split_cols<<<dim3((unsigned)(hnp / 64), (unsigned)P), 256, kSplitColsSmem, stream>>>(sb);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+
+  GemmArgs ga;
+  std::memset(&ga, 0, sizeof(ga));
+  if (!encode_bf16(&ga.tmA, DX, (int64_t)P * kS * hmp, hkp) || !encode_bf16(&ga.tmB, DV, (int64_t)P * kS * hnp, hkp))
+    return cudaErrorInvalidValue;
+  ga.t_hi = thi; ga.t_lo = tlo;
+  ga.P = P;
+  ga.tiles_m = (int)(hmp / kTM); ga.tiles_n = (int)(hnp / kTN);
+  ga.nkb = (int)(hkp / kTK);
+  ga.h_mp = hmp; ga.h_np = hnp;
+  const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n;
+  const int grid = (int)std::min<int64_t>(sms, units);
+  void* gargs[] = {&ga};
+  e = cudaLaunchKernel((const void*)oz_gemm, dim3(grid), dim3(kThreads), gargs, oz_gemm_smem(), stream);
+  if (e != cudaSuccess) return e;
+
+  RecombineArgs ra;
+  ra.C = C; ra.ldc = ldc; ra.m = m; ra.n = n;
+  ra.hm = hm; ra.hn = hn; ra.h_mp = hmp; ra.h_np = hnp;
+  ra.levels = levels; ra.P = P;
+  ra.t_hi = thi; ra.t_lo = tlo; ra.e = ex; ra.f = fx;
+  const int64_t total = hm * hn * (1LL << (2 * levels));
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)sms * 32);
+  oz_recombine_scatter<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, stream>>>(ra);
+  return cudaGetLastError();
+}
+
+}  // namespace sgb

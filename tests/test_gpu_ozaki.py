@@ -1,0 +1,94 @@
+"""GPU parity of the split-precision path (dtype STRASSEN_F64_OZ_BF16, tensor-core BF16
+slice products) against the oracle of the same scheme, through the C ABI.
+
+The slice products are exact integers on both sides and the recombination is one
+correctly rounded conversion followed by the C additions in product order, so the GPU
+result must equal the oracle bit for bit on any finite input.  Against the plain FP64
+oracle the error is stated per input spread sigma and held to the normwise FP64
+tolerance for sigma = 0.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from oracle import ozaki
+import paper_1605_01078_gb300 as sg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+OZ = "oz_bf16"
+TOL = {0: 1e-13, 1: 1e-13, 2: 1e-12}
+
+
+def effective_levels(levels, m, n, k):
+    """The library clamps levels while 2^levels exceeds min(m, n, k)."""
+    while levels > 0 and (1 << levels) > min(m, n, k):
+        levels -= 1
+    return levels
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def run(A, B, C, levels):
+    dC = dev(C)
+    sg.gemm(dev(A), dev(B), dC, levels=levels, variant="ABC", dtype=OZ)
+    torch.cuda.synchronize()
+    assert sg.strassen_device_status(0) == 0
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("m,n,k", [(16, 16, 16), (130, 70, 150), (300, 260, 2100), (1, 1, 1), (5, 129, 3)])
+def test_bit_exact_against_the_scheme_oracle(levels, m, n, k):
+    A, B, C = W.uniform(m, k, 1), W.uniform(k, n, 2), W.uniform(m, n, 3)
+    ref = ozaki.gemm(A, B, C, effective_levels(levels, m, n, k))
+    got = run(A, B, C, levels)
+    assert np.array_equal(got, ref), float(np.max(np.abs(got - ref)))
+
+
+@pytest.mark.parametrize("sigma", [4, 10])
+def test_bit_exact_with_spread_exponents(sigma):
+    A, B, C = W.scaled(200, 300, 4, sigma), W.scaled(300, 150, 5, sigma), W.scaled(200, 150, 6, sigma)
+    for levels in (0, 1):
+        assert np.array_equal(run(A, B, C, levels), ozaki.gemm(A, B, C, levels))
+
+
+def test_integer_inputs_exact():
+    A, B, C = W.integer(100, 90, 7), W.integer(90, 80, 8), W.integer(100, 80, 9)
+    for levels in (0, 1, 2):
+        assert np.array_equal(run(A, B, C, levels), C + A @ B)
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_fp64_tolerance_config_1024(levels):
+    n = 1024
+    A, B, C = W.uniform(n, n, 0), W.uniform(n, n, 1), np.zeros((n, n))
+    got = run(A, B, C, levels)
+    ref = C.copy()
+    oracle.gemm(A, B, ref)
+    den = float(np.max(np.sum(np.abs(A), axis=1))) * float(np.max(np.abs(B)))
+    assert float(np.max(np.abs(got - ref))) / den <= TOL[levels]
+
+
+@pytest.mark.parametrize("levels", [0, 1])
+def test_full_size_sampled(levels):
+    n = 8192
+    A, B, C = W.uniform(n, n, 100), W.uniform(n, n, 101), W.uniform(n, n, 102)
+    got = run(A, B, C, levels)
+    rows, cols = W.sample_indices(n, n, 256, 3)
+    ref = oracle.gemm_sampled(A, B, C, rows, cols)
+    den = float(np.max(np.sum(np.abs(A), axis=1))) * float(np.max(np.abs(B)))
+    assert float(np.max(np.abs(got[rows, cols] - ref))) / den <= TOL[levels]
+
+
+def test_int8_slices_not_built():
+    A = dev(np.ones((4, 4)))
+    C = dev(np.zeros((4, 4)))
+    st = sg.strassen_gemm(4, 4, 4, A.data_ptr(), 4, A.data_ptr(), 4, C.data_ptr(), 4, 0, 0,
+                          sg.STRASSEN_F64_OZ_INT8, 0)
+    assert st == -5
