@@ -176,11 +176,15 @@ STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
  * builds its performance model for.  In order of precedence it returns
  *   1. the exhaustive-measurement record for exactly this shape and dtype, if one was
  *      stored with strassen_tune_record();
- *   2. the analytic model's argmin (strassen_model_seconds) otherwise.
- * Fewer levels win ties within 1 %.
+ *   2. the argmin of the learned selector's predictions, if a network was loaded with
+ *      strassen_selector_load() (one small kernel launch on a library stream, then a
+ *      wait for its result);
+ *   3. the analytic model's argmin (strassen_model_seconds) otherwise (FP64), or
+ *      classical slices (split-precision dtypes).
+ * The model prefers fewer levels on ties within 1 %.
  *
  *   levels, variant, tile_id   outputs (host pointers, non-NULL).
- * Returns STRASSEN_OK or a negative status.  Host-only; launches nothing.
+ * Returns STRASSEN_OK or a negative status.
  */
 STRASSEN_API int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype,
                                  int* levels, strassen_variant* variant, int* tile_id);
@@ -204,6 +208,37 @@ STRASSEN_API int strassen_tune_clear(void);
  */
 STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int levels,
                                            strassen_variant variant);
+
+/*
+ * The learned selector (not in the paper; it stands in for the analytic model of
+ * Section 4.2).  A multilayer perceptron 6 -> 64 -> 64 -> 7 (FP32, ReLU) maps the
+ * features ((log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype one-hot) to the
+ * predicted log2 seconds of the 7 candidates (levels, variant): 0 (0, ABC),
+ * 1 (1, ABC), 2 (1, AB), 3 (1, Naive), 4 (2, ABC), 5 (2, AB), 6 (2, Naive).  Its
+ * parameters are one float vector of strassen_mlp_param_count() entries:
+ * [W1 (64x6 row-major), b1 (64), W2 (64x64), b2 (64), W3 (7x64), b3 (7)].
+ *
+ * strassen_mlp_forward   Y[batch][7] = network(X[batch][6]); all DEVICE pointers.
+ * strassen_mlp_loss_grad grad = d/dparams of sum mask (Y - T)^2 / mask_sum over the
+ *                        batch (X [batch][6], T and mask [batch][7], DEVICE); grad is
+ *                        overwritten.  mask_sum > 0 is the sum of mask.
+ * strassen_mlp_adam      one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1)
+ *                        on `count` parameters with moment buffers m, v (DEVICE).
+ * strassen_selector_load copies a trained parameter vector (HOST) to the current device
+ *                        and makes strassen_select() use it; strassen_selector_clear
+ *                        forgets it.
+ * All return STRASSEN_OK or a negative status; the kernels run on `stream`.
+ */
+STRASSEN_API int strassen_mlp_param_count(void);
+STRASSEN_API int strassen_mlp_forward(const float* params, const float* X, int batch, float* Y,
+                                      strassen_stream_t stream);
+STRASSEN_API int strassen_mlp_loss_grad(const float* params, const float* X, const float* T,
+                                        const float* mask, int batch, float mask_sum, float* grad,
+                                        strassen_stream_t stream);
+STRASSEN_API int strassen_mlp_adam(float* params, const float* grad, float* m, float* v, int count,
+                                   int step, float lr, strassen_stream_t stream);
+STRASSEN_API int strassen_selector_load(const float* params_host, int count);
+STRASSEN_API int strassen_selector_clear(void);
 
 /*
  * strassen_workspace_size -- bytes of stream-ordered temporaries a strassen_gemm call

@@ -56,6 +56,12 @@ SIGNATURES = {
     "strassen_tune_record": (_I, [_I64, _I64, _I64, _I, _I, _I, _I]),
     "strassen_tune_clear": (_I, []),
     "strassen_model_seconds": (ctypes.c_double, [_I64, _I64, _I64, _I, _I]),
+    "strassen_mlp_param_count": (_I, []),
+    "strassen_mlp_forward": (_I, [_P, _P, _I, _P, _P]),
+    "strassen_mlp_loss_grad": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _P, _P]),
+    "strassen_mlp_adam": (_I, [_P, _P, _P, _P, _I, _I, ctypes.c_float, _P]),
+    "strassen_selector_load": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
+    "strassen_selector_clear": (_I, []),
     "strassen_check_wait_timeout": (_I, [_I64, _P]),
 }
 
@@ -129,6 +135,30 @@ def strassen_tune_clear() -> int:
 
 def strassen_model_seconds(m, n, k, levels, variant) -> float:
     return lib().strassen_model_seconds(m, n, k, levels, variant)
+
+
+def strassen_mlp_param_count() -> int:
+    return lib().strassen_mlp_param_count()
+
+
+def strassen_mlp_forward(params, X, batch, Y, stream) -> int:
+    return lib().strassen_mlp_forward(params, X, batch, Y, stream)
+
+
+def strassen_mlp_loss_grad(params, X, T, mask, batch, mask_sum, grad, stream) -> int:
+    return lib().strassen_mlp_loss_grad(params, X, T, mask, batch, mask_sum, grad, stream)
+
+
+def strassen_mlp_adam(params, grad, m, v, count, step, lr, stream) -> int:
+    return lib().strassen_mlp_adam(params, grad, m, v, count, step, lr, stream)
+
+
+def strassen_selector_load(params_host, count) -> int:
+    return lib().strassen_selector_load(params_host, count)
+
+
+def strassen_selector_clear() -> int:
+    return lib().strassen_selector_clear()
 
 
 def strassen_workspace_size(m, n, k, levels, variant, dtype) -> int:

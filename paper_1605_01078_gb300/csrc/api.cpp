@@ -278,7 +278,17 @@ int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* 
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
   int lv = 0, var = STRASSEN_ABC, tile = 0;
-  if (!record_lookup(m, n, k, (int)dtype, &lv, &var, &tile)) {
+  int cand = -1;
+  if (record_lookup(m, n, k, (int)dtype, &lv, &var, &tile)) {
+    // exhaustive measurement
+  } else if (m > 0 && n > 0 && k > 0 && mlp_select(m, n, k, (int)dtype, &cand)) {
+    static const int kLv[7] = {0, 1, 1, 1, 2, 2, 2};
+    static const int kVar[7] = {STRASSEN_ABC, STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE,
+                                STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE};
+    lv = kLv[cand];
+    var = kVar[cand];
+    tile = 0;
+  } else {
     if (dtype == STRASSEN_F64) {
       model_select(m, n, k, &lv, &var);
     } else {  // split precision: tensor-core products, no FP64 model; classical slices

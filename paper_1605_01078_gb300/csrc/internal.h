@@ -108,6 +108,11 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                       double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream);
 int ozaki_device_status();
 
+// Learned selector (mlp.cu): argmin of the loaded MLP's predictions for a shape;
+// false when no network is loaded (or it lives on another device).  Candidate c maps
+// to (levels, variant): 0 (0,ABC) 1 (1,ABC) 2 (1,AB) 3 (1,Naive) 4 (2,ABC) 5 (2,AB) 6 (2,Naive).
+bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate);
+
 // Selection (select.cpp): analytic time model, its argmin, and the exhaustive records.
 double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant);
 void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant);

@@ -1,0 +1,263 @@
+// Learned variant selector: a small MLP (6 -> 64 -> 64 -> 7, FP32, ReLU) that predicts
+// the log2 run time of each member of the family -- classical, and 1 / 2 levels of ABC,
+// AB and Naive -- from log2 m, log2 n, log2 k and the dtype.  It stands in for the
+// analytic performance model of Section 4.2 when choosing the implementation.
+//
+// Hand-written kernels: forward, loss gradient (forward + reverse mode per sample,
+// per-block gradient sums in shared memory, one atomic add per parameter per block),
+// Adam, and the single-shape selection used by strassen_select().
+//
+// Parameter vector (float): [W1 (64x6, row-major), b1 (64), W2 (64x64), b2 (64),
+// W3 (7x64), b3 (7)].  Loss: masked mean squared error over measured candidates.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace sgb {
+namespace {
+
+constexpr int kIn = 6, kH = 64, kOut = 7;
+constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
+              ob3 = oW3 + kOut * kH, kParams = ob3 + kOut;
+constexpr int kBlock = 64;  // one thread per hidden unit
+
+// Forward pass of one sample by a block of kH threads; x, h1, h2, z1, z2 in shared
+// memory; returns with y[0..kOut) in shared memory.
+__device__ void sample_forward(const float* P, const float* x, float* z1, float* h1, float* z2, float* h2,
+                               float* y) {
+  const int h = threadIdx.x;
+  float acc = P[ob1 + h];
+  for (int i = 0; i < kIn; ++i) acc += P[oW1 + h * kIn + i] * x[i];
+  z1[h] = acc;
+  h1[h] = acc > 0.f ? acc : 0.f;
+  __syncthreads();
+  acc = P[ob2 + h];
+  for (int j = 0; j < kH; ++j) acc += P[oW2 + h * kH + j] * h1[j];
+  z2[h] = acc;
+  h2[h] = acc > 0.f ? acc : 0.f;
+  __syncthreads();
+  if (h < kOut) {
+    float o = P[ob3 + h];
+    for (int j = 0; j < kH; ++j) o += P[oW3 + h * kH + j] * h2[j];
+    y[h] = o;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlock) mlp_forward_kernel(const float* __restrict__ params,
+                                                             const float* __restrict__ X, int batch,
+                                                             float* __restrict__ Y) {
+  __shared__ float P[kParams];
+  __shared__ float x[kIn], z1[kH], h1[kH], z2[kH], h2[kH], y[kOut];
+  for (int i = threadIdx.x; i < kParams; i += kBlock) P[i] = params[i];
+  __syncthreads();
+  for (int s = blockIdx.x; s < batch; s += gridDim.x) {
+    if (threadIdx.x < kIn) x[threadIdx.x] = X[s * kIn + threadIdx.x];
+    __syncthreads();
+    sample_forward(P, x, z1, h1, z2, h2, y);
+    if (threadIdx.x < kOut) Y[s * kOut + threadIdx.x] = y[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// grad += d loss / d params over the block's samples; loss = sum mask (y - t)^2 * inv.
+__global__ void __launch_bounds__(kBlock) mlp_grad_kernel(const float* __restrict__ params,
+                                                          const float* __restrict__ X,
+                                                          const float* __restrict__ T,
+                                                          const float* __restrict__ M, int batch, float inv,
+                                                          float* __restrict__ grad) {
+  __shared__ float P[kParams];
+  __shared__ float G[kParams];
+  __shared__ float x[kIn], z1[kH], h1[kH], z2[kH], h2[kH], y[kOut], dy[kOut], dz2[kH];
+  const int h = threadIdx.x;
+  for (int i = h; i < kParams; i += kBlock) {
+    P[i] = params[i];
+    G[i] = 0.f;
+  }
+  __syncthreads();
+  for (int s = blockIdx.x; s < batch; s += gridDim.x) {
+    if (h < kIn) x[h] = X[s * kIn + h];
+    __syncthreads();
+    sample_forward(P, x, z1, h1, z2, h2, y);
+    if (h < kOut) dy[h] = 2.f * M[s * kOut + h] * (y[h] - T[s * kOut + h]) * inv;
+    __syncthreads();
+    // layer 3: thread h owns column h of W3 and row h of the hidden state
+    float dh2 = 0.f;
+    for (int c = 0; c < kOut; ++c) {
+      G[oW3 + c * kH + h] += dy[c] * h2[h];
+      dh2 += dy[c] * P[oW3 + c * kH + h];
+    }
+    if (h < kOut) G[ob3 + h] += dy[h];
+    const float d2 = z2[h] > 0.f ? dh2 : 0.f;
+    dz2[h] = d2;
+    __syncthreads();
+    // layer 2: row h of W2
+    for (int j = 0; j < kH; ++j) G[oW2 + h * kH + j] += d2 * h1[j];
+    G[ob2 + h] += d2;
+    float dh1 = 0.f;
+    for (int r = 0; r < kH; ++r) dh1 += dz2[r] * P[oW2 + r * kH + h];
+    const float d1 = z1[h] > 0.f ? dh1 : 0.f;
+    for (int i = 0; i < kIn; ++i) G[oW1 + h * kIn + i] += d1 * x[i];
+    G[ob1 + h] += d1;
+    __syncthreads();
+  }
+  for (int i = h; i < kParams; i += kBlock) atomicAdd(&grad[i], G[i]);
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float lr, float c1, float c2) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float mi = b1 * m[i] + (1.f - b1) * g[i];
+    const float vi = b2 * v[i] + (1.f - b2) * g[i] * g[i];
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+struct SelectArgs {
+  float x[kIn];
+  unsigned valid;  // bit c set: candidate c may be chosen
+};
+
+__global__ void __launch_bounds__(kBlock) mlp_select_kernel(const float* __restrict__ params,
+                                                            const __grid_constant__ SelectArgs a,
+                                                            int* __restrict__ out) {
+  __shared__ float P[kParams];
+  __shared__ float x[kIn], z1[kH], h1[kH], z2[kH], h2[kH], y[kOut];
+  for (int i = threadIdx.x; i < kParams; i += kBlock) P[i] = params[i];
+  if (threadIdx.x < kIn) x[threadIdx.x] = a.x[threadIdx.x];
+  __syncthreads();
+  sample_forward(P, x, z1, h1, z2, h2, y);
+  if (threadIdx.x == 0) {
+    int best = -1;
+    for (int c = 0; c < kOut; ++c)
+      if (((a.valid >> c) & 1u) && (best < 0 || y[c] < y[best])) best = c;
+    *out = best;
+  }
+}
+
+// ---------------------------------------------------------------- selector state
+
+std::mutex g_mlp_mu;
+float* g_sel_params = nullptr;  // device copy of the loaded network (device 0 of the loader)
+int* g_sel_out = nullptr;
+cudaStream_t g_sel_stream = nullptr;
+int g_sel_device = -1;
+
+int grid_for_batch(int batch) { return batch < 1 ? 1 : (batch < 1024 ? batch : 1024); }
+
+}  // namespace
+
+void mlp_features(int64_t m, int64_t n, int64_t k, int dtype, float* x) {
+  x[0] = (float)((std::log2((double)m) - 11.0) / 3.0);
+  x[1] = (float)((std::log2((double)n) - 11.0) / 3.0);
+  x[2] = (float)((std::log2((double)k) - 11.0) / 3.0);
+  x[3] = dtype == 0 ? 1.f : 0.f;
+  x[4] = dtype == 1 ? 1.f : 0.f;
+  x[5] = dtype == 2 ? 1.f : 0.f;
+}
+
+bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate) {
+  std::lock_guard<std::mutex> lock(g_mlp_mu);
+  if (!g_sel_params) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != g_sel_device) {
+    cudaGetLastError();
+    return false;
+  }
+  SelectArgs a;
+  mlp_features(m, n, k, dtype, a.x);
+  a.valid = dtype == STRASSEN_F64 ? 0x7Fu : 0x13u;  // split precision: levels 0, 1, 2 of ABC
+  mlp_select_kernel<<<1, kBlock, 0, g_sel_stream>>>(g_sel_params, a, g_sel_out);
+  int host = -1;
+  if (cudaMemcpyAsync(&host, g_sel_out, sizeof(int), cudaMemcpyDeviceToHost, g_sel_stream) != cudaSuccess ||
+      cudaStreamSynchronize(g_sel_stream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (host < 0 || host >= kOut) return false;
+  *candidate = host;
+  return true;
+}
+
+}  // namespace sgb
+
+using namespace sgb;
+
+extern "C" {
+
+int strassen_mlp_param_count(void) { return kParams; }
+
+int strassen_mlp_forward(const float* params, const float* X, int batch, float* Y, strassen_stream_t stream) {
+  if (batch < 0) return STRASSEN_ERR_ARG;
+  if (batch == 0) return STRASSEN_OK;
+  if (!params || !X || !Y) return STRASSEN_ERR_NULL;
+  mlp_forward_kernel<<<grid_for_batch(batch), kBlock, 0, (cudaStream_t)stream>>>(params, X, batch, Y);
+  return cudaGetLastError() == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA;
+}
+
+int strassen_mlp_loss_grad(const float* params, const float* X, const float* T, const float* mask, int batch,
+                           float mask_sum, float* grad, strassen_stream_t stream) {
+  if (batch < 0 || !(mask_sum > 0.f)) return STRASSEN_ERR_ARG;
+  if (!params || !X || !T || !mask || !grad) return STRASSEN_ERR_NULL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(grad, 0, sizeof(float) * kParams, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  if (batch == 0) return STRASSEN_OK;
+  mlp_grad_kernel<<<grid_for_batch(batch) < 152 ? grid_for_batch(batch) : 152, kBlock, 0, s>>>(
+      params, X, T, mask, batch, 1.f / mask_sum, grad);
+  return cudaGetLastError() == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA;
+}
+
+int strassen_mlp_adam(float* params, const float* grad, float* m, float* v, int count, int step, float lr,
+                      strassen_stream_t stream) {
+  if (count < 0 || step < 1) return STRASSEN_ERR_ARG;
+  if (!params || !grad || !m || !v) return STRASSEN_ERR_NULL;
+  const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
+  adam_kernel<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, grad, m, v, count, lr, c1, c2);
+  return cudaGetLastError() == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA;
+}
+
+int strassen_selector_load(const float* params_host, int count) {
+  if (count != kParams) return STRASSEN_ERR_ARG;
+  if (!params_host) return STRASSEN_ERR_NULL;
+  std::lock_guard<std::mutex> lock(g_mlp_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return STRASSEN_ERR_CUDA;
+  if (!g_sel_params) {
+    if (cudaMalloc(&g_sel_params, sizeof(float) * kParams) != cudaSuccess ||
+        cudaMalloc(&g_sel_out, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&g_sel_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return STRASSEN_ERR_ALLOC;
+    }
+    g_sel_device = dev;
+  } else if (dev != g_sel_device) {
+    return STRASSEN_ERR_ARG;
+  }
+  if (cudaMemcpy(g_sel_params, params_host, sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess)
+    return STRASSEN_ERR_CUDA;
+  return STRASSEN_OK;
+}
+
+int strassen_selector_clear(void) {
+  std::lock_guard<std::mutex> lock(g_mlp_mu);
+  if (g_sel_params) {
+    cudaStreamSynchronize(g_sel_stream);
+    cudaFree(g_sel_params);
+    cudaFree(g_sel_out);
+    cudaStreamDestroy(g_sel_stream);
+    g_sel_params = nullptr;
+    g_sel_out = nullptr;
+    g_sel_stream = nullptr;
+    g_sel_device = -1;
+  }
+  return STRASSEN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,295 @@
+"""Exhaustive autotuner and learned-selector training for the Strassen library.
+
+The family of Section 4.1 has one member per (levels, variant); which one is fastest
+depends on the shape (the paper draws this conclusion from its model and its
+measurements).  This module
+
+* times the candidates of a shape through the C ABI (``measure``) -- the exhaustive
+  search, whose winners ``record`` hands to the library (strassen_tune_record);
+* trains the selector MLP on such timings with the library's own CUDA kernels
+  (strassen_mlp_loss_grad / strassen_mlp_adam), loads it (strassen_selector_load), and
+* evaluates choices by regret t(chosen) / t(best) - 1 against exhaustive timing, for
+  the MLP, the analytic model (strassen_model_seconds) and fixed rules.
+
+Python only drives the calls; all arithmetic of the network runs in the CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import math
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _binding as B
+
+# Candidate c -> (levels, variant), the order of the network's outputs.
+CANDIDATES: List[Tuple[int, int]] = [(0, B.STRASSEN_ABC), (1, B.STRASSEN_ABC), (1, B.STRASSEN_AB),
+                                     (1, B.STRASSEN_NAIVE), (2, B.STRASSEN_ABC), (2, B.STRASSEN_AB),
+                                     (2, B.STRASSEN_NAIVE)]
+VALID = {B.STRASSEN_F64: [0, 1, 2, 3, 4, 5, 6], B.STRASSEN_F64_OZ_BF16: [0, 1, 4]}
+DTYPE_NAME = {B.STRASSEN_F64: "f64", B.STRASSEN_F64_OZ_BF16: "oz_bf16"}
+
+
+def features(m, n, k, dtype) -> np.ndarray:
+    """Network inputs (float32): (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, one-hot dtype."""
+    m, n, k, dtype = (np.atleast_1d(np.asarray(v)) for v in (m, n, k, dtype))
+    x = np.zeros((m.size, 6), dtype=np.float32)
+    x[:, 0] = (np.log2(m) - 11.0) / 3.0
+    x[:, 1] = (np.log2(n) - 11.0) / 3.0
+    x[:, 2] = (np.log2(k) - 11.0) / 3.0
+    x[np.arange(m.size), 3 + dtype.astype(int)] = 1.0
+    return x
+
+
+class Timer:
+    """Times candidates on one preallocated set of operand buffers."""
+
+    def __init__(self, max_elems_a: int, max_elems_b: int, max_elems_c: int):
+        import torch
+        self.torch = torch
+        self.A = torch.rand(max_elems_a, dtype=torch.float64, device="cuda") * 2 - 1
+        self.B = torch.rand(max_elems_b, dtype=torch.float64, device="cuda") * 2 - 1
+        self.C = torch.zeros(max_elems_c, dtype=torch.float64, device="cuda")
+        self.stream = torch.cuda.current_stream()
+        self.e0 = torch.cuda.Event(enable_timing=True)
+        self.e1 = torch.cuda.Event(enable_timing=True)
+
+    def _call(self, m, n, k, levels, variant, dtype):
+        st = B.strassen_gemm(m, n, k, self.A.data_ptr(), k, self.B.data_ptr(), n, self.C.data_ptr(), n,
+                             levels, variant, dtype, self.stream.cuda_stream)
+        if st != 0:
+            raise B.StrassenError(st, "strassen_gemm")
+
+    def time(self, m, n, k, levels, variant, dtype, min_seconds=2e-3, max_reps=20) -> float:
+        """Median-free best-effort time: one untimed call, then repeated timed calls until
+        min_seconds of work (or max_reps); returns seconds per call."""
+        self._call(m, n, k, levels, variant, dtype)
+        reps, total = 0, 0.0
+        while reps < max_reps and (total < min_seconds or reps == 0):
+            self.e0.record(self.stream)
+            self._call(m, n, k, levels, variant, dtype)
+            self.e1.record(self.stream)
+            self.e1.synchronize()
+            total += self.e0.elapsed_time(self.e1) / 1e3
+            reps += 1
+        return total / reps
+
+
+def measure(shapes: Sequence[Tuple[int, int, int]], dtype: int, timer: Timer,
+            candidates: Optional[Sequence[int]] = None) -> List[Dict]:
+    """Exhaustive timing: one row per shape with the seconds of every valid candidate."""
+    cands = list(VALID[dtype] if candidates is None else candidates)
+    rows = []
+    for (m, n, k) in shapes:
+        times = [math.nan] * len(CANDIDATES)
+        for c in cands:
+            lv, var = CANDIDATES[c]
+            times[c] = timer.time(m, n, k, lv, var, dtype)
+        rows.append({"m": int(m), "n": int(n), "k": int(k), "dtype": int(dtype), "times": times})
+    return rows
+
+
+def best_of(row) -> int:
+    t = np.array(row["times"], dtype=np.float64)
+    return int(np.nanargmin(t))
+
+
+def record(rows) -> None:
+    """Hand the exhaustive winners to the library's selection table."""
+    for r in rows:
+        lv, var = CANDIDATES[best_of(r)]
+        st = B.strassen_tune_record(r["m"], r["n"], r["k"], r["dtype"], lv, var, 0)
+        if st != 0:
+            raise B.StrassenError(st, "strassen_tune_record")
+
+
+def arrays(rows):
+    """Network inputs X, targets T = log2 seconds, and the mask of measured candidates."""
+    X = features([r["m"] for r in rows], [r["n"] for r in rows], [r["k"] for r in rows],
+                 [r["dtype"] for r in rows])
+    t = np.array([r["times"] for r in rows], dtype=np.float64)
+    mask = np.isfinite(t).astype(np.float32)
+    T = np.where(np.isfinite(t), np.log2(np.where(np.isfinite(t), t, 1.0)), 0.0).astype(np.float32)
+    return X, T, mask
+
+
+def init_params(seed: int) -> np.ndarray:
+    """He-uniform weights, zero biases (float32), in the library's parameter order."""
+    g = np.random.Generator(np.random.Philox(seed))
+    shapes = [(64, 6), (64,), (64, 64), (64,), (7, 64), (7,)]
+    parts = []
+    for shp in shapes:
+        if len(shp) == 2:
+            lim = math.sqrt(6.0 / shp[1])
+            parts.append(g.uniform(-lim, lim, size=shp).ravel())
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(rows, steps: int = 3000, lr: float = 3e-3, seed: int = 0, params: Optional[np.ndarray] = None):
+    """Full-batch Adam on the masked MSE of log2 times, entirely in the library's
+    kernels.  Returns (parameters as numpy float32, loss history: step 0, then every
+    100 steps)."""
+    import torch
+    X, T, mask = arrays(rows)
+    n_par = B.strassen_mlp_param_count()
+    p0 = init_params(seed) if params is None else np.asarray(params, dtype=np.float32)
+    assert p0.size == n_par
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dX, dT, dM = dev(X), dev(T), dev(mask)
+    P = dev(p0)
+    G = torch.zeros_like(P)
+    Mo = torch.zeros_like(P)
+    V = torch.zeros_like(P)
+    Y = torch.empty((len(rows), 7), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    msum = float(mask.sum())
+    hist = []
+
+    def current_loss():
+        B.strassen_mlp_forward(P.data_ptr(), dX.data_ptr(), len(rows), Y.data_ptr(), s)
+        return float(((Y - dT) ** 2 * dM).sum() / msum)
+
+    hist.append((0, current_loss()))
+    for step in range(1, steps + 1):
+        st = B.strassen_mlp_loss_grad(P.data_ptr(), dX.data_ptr(), dT.data_ptr(), dM.data_ptr(), len(rows), msum,
+                                      G.data_ptr(), s)
+        if st != 0:
+            raise B.StrassenError(st, "strassen_mlp_loss_grad")
+        st = B.strassen_mlp_adam(P.data_ptr(), G.data_ptr(), Mo.data_ptr(), V.data_ptr(), n_par, step, lr, s)
+        if st != 0:
+            raise B.StrassenError(st, "strassen_mlp_adam")
+        if step % 100 == 0 or step == steps:
+            hist.append((step, current_loss()))
+    return P.cpu().numpy(), hist
+
+
+def predict(params: np.ndarray, rows) -> np.ndarray:
+    """Predicted log2 seconds [rows, 7] from the library's forward kernel."""
+    import torch
+    X, _, _ = arrays(rows)
+    P = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    dX = torch.from_numpy(X).cuda()
+    Y = torch.empty((len(rows), 7), dtype=torch.float32, device="cuda")
+    st = B.strassen_mlp_forward(P.data_ptr(), dX.data_ptr(), len(rows), Y.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    if st != 0:
+        raise B.StrassenError(st, "strassen_mlp_forward")
+    return Y.cpu().numpy()
+
+
+def choose_mlp(params, rows) -> List[int]:
+    Y = predict(params, rows)
+    out = []
+    for r, y in zip(rows, Y):
+        valid = VALID[r["dtype"]]
+        out.append(int(valid[int(np.argmin(y[valid]))]))
+    return out
+
+
+def choose_model(rows) -> List[int]:
+    """Argmin of the analytic model (FP64 candidates); split precision: classical."""
+    out = []
+    for r in rows:
+        if r["dtype"] != B.STRASSEN_F64:
+            out.append(0)
+            continue
+        t = [B.strassen_model_seconds(r["m"], r["n"], r["k"], lv, var) for (lv, var) in CANDIDATES]
+        out.append(int(np.argmin(t)))
+    return out
+
+
+def choose_fixed(rows, candidate: int) -> List[int]:
+    return [candidate if candidate in VALID[r["dtype"]] else 0 for r in rows]
+
+
+def regret(rows, choices) -> Dict[str, float]:
+    """Mean and 95th percentile of t(chosen)/t(best) - 1 over the rows."""
+    reg = []
+    for r, c in zip(rows, choices):
+        t = np.array(r["times"], dtype=np.float64)
+        reg.append(t[c] / np.nanmin(t) - 1.0)
+    reg = np.array(reg)
+    return {"mean": float(np.mean(reg)), "p95": float(np.percentile(reg, 95)), "max": float(np.max(reg)),
+            "n": int(reg.size)}
+
+
+def load_selector(params: np.ndarray) -> None:
+    arr = np.ascontiguousarray(params, dtype=np.float32)
+    st = B.strassen_selector_load(arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), arr.size)
+    if st != 0:
+        raise B.StrassenError(st, "strassen_selector_load")
+
+
+def save_rows(path: str, rows) -> None:
+    with open(path, "w") as fh:
+        json.dump(rows, fh)
+
+
+def load_rows(path: str):
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def main(argv=None) -> int:
+    """Exhaustive timing of seeded random shapes, selector training and held-out
+    evaluation; writes rows, parameters and a regret summary as JSON into --out."""
+    import argparse
+    import os
+    import sys
+    import time
+    ap = argparse.ArgumentParser(prog="python -m paper_1605_01078_gb300.tune")
+    ap.add_argument("--train", type=int, default=700, help="FP64 training shapes (seed 1)")
+    ap.add_argument("--heldout", type=int, default=1000, help="FP64 held-out shapes (seed 2)")
+    ap.add_argument("--oz-train", type=int, default=300, help="split-precision training shapes (seed 3)")
+    ap.add_argument("--oz-heldout", type=int, default=200, help="split-precision held-out shapes (seed 4)")
+    ap.add_argument("--lo", type=int, default=256)
+    ap.add_argument("--hi", type=int, default=16384)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import workloads as W
+    os.makedirs(a.out, exist_ok=True)
+    timer = Timer(a.hi * a.hi, a.hi * a.hi, a.hi * a.hi)
+    t0 = time.time()
+    f64 = B.STRASSEN_F64
+    oz = B.STRASSEN_F64_OZ_BF16
+    train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, timer)
+    train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, timer)
+    t_train = time.time() - t0
+    held_rows = measure(W.loguniform_shapes(a.heldout, 2, a.lo, a.hi), f64, timer)
+    held_oz = measure(W.loguniform_shapes(a.oz_heldout, 4, a.lo, a.hi), oz, timer)
+    t_held = time.time() - t0 - t_train
+    params, hist = train(train_rows, steps=a.steps, lr=3e-3, seed=0)
+    summary = {"timings_train": int(sum(np.isfinite(r["times"]).sum() for r in train_rows)),
+               "shapes_train": len(train_rows), "shapes_heldout_f64": len(held_rows),
+               "shapes_heldout_oz": len(held_oz), "seconds_measuring": [t_train, t_held],
+               "loss_history": hist}
+    for name, rows in (("f64", held_rows), ("oz_bf16", held_oz)):
+        summary[name] = {
+            "mlp": regret(rows, choose_mlp(params, rows)),
+            "analytic_model": regret(rows, choose_model(rows)),
+            "always_1L_ABC": regret(rows, choose_fixed(rows, 1)),
+            "always_2L_ABC": regret(rows, choose_fixed(rows, 4)),
+            "classical": regret(rows, choose_fixed(rows, 0)),
+            "exhaustive": regret(rows, [best_of(r) for r in rows]),
+            "best_counts": {str(c): int(sum(best_of(r) == c for r in rows)) for c in range(7)},
+        }
+    save_rows(os.path.join(a.out, "selector_train_rows.json"), train_rows)
+    save_rows(os.path.join(a.out, "selector_heldout_rows.json"), held_rows + held_oz)
+    with open(os.path.join(a.out, "selector_params.json"), "w") as fh:
+        json.dump([float(v) for v in params], fh)
+    with open(os.path.join(a.out, "selector_summary.json"), "w") as fh:
+        json.dump(summary, fh, indent=1)
+    print(json.dumps({k: summary[k] for k in ("f64", "oz_bf16")}, indent=1))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

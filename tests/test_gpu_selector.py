@@ -1,0 +1,40 @@
+"""The learned selector on live timings: exhaustive measurement of a small seeded set
+of shapes, training with the library's kernels, and regret on held-out shapes against
+the analytic model and a fixed rule."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1605_01078_gb300 as sg
+from paper_1605_01078_gb300 import tune
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_selector_on_live_timings():
+    train_shapes = W.loguniform_shapes(48, seed=11, lo=128, hi=3072)
+    held_shapes = W.loguniform_shapes(32, seed=12, lo=128, hi=3072)
+    timer = tune.Timer(3072 * 3072, 3072 * 3072, 3072 * 3072)
+    train_rows = tune.measure(train_shapes, sg.STRASSEN_F64, timer)
+    held_rows = tune.measure(held_shapes, sg.STRASSEN_F64, timer)
+    params, hist = tune.train(train_rows, steps=2000, lr=3e-3, seed=0)
+    assert hist[-1][1] < hist[0][1]
+    r_mlp = tune.regret(held_rows, tune.choose_mlp(params, held_rows))
+    r_model = tune.regret(held_rows, tune.choose_model(held_rows))
+    r_abc1 = tune.regret(held_rows, tune.choose_fixed(held_rows, 1))
+    r_best = tune.regret(held_rows, [tune.best_of(r) for r in held_rows])
+    print("regret mlp", r_mlp, "model", r_model, "always 1L ABC", r_abc1)
+    assert r_best["max"] == 0.0
+    # the trained network beats the fixed rule and stays within a few percent of the best
+    assert r_mlp["mean"] <= r_abc1["mean"]
+    assert r_mlp["mean"] < 0.10
+    # loading it makes strassen_select follow it
+    tune.load_selector(params)
+    try:
+        for r, c in zip(held_rows[:8], tune.choose_mlp(params, held_rows[:8])):
+            lv, var, _ = sg.strassen_select(r["m"], r["n"], r["k"], sg.STRASSEN_F64)
+            assert (lv, var) == tune.CANDIDATES[c]
+    finally:
+        sg.strassen_selector_clear()
