@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
     return ap.parse_args()
 
 
@@ -188,6 +189,43 @@ def bench_batched(sg, W, torch, reps=3):
             "value": flops / t_graph / 1e9, "unit": UNIT, "ms": t_graph * 1e3,
             "loop_of_classical": {"value": flops / t_loop / 1e9, "ms": t_loop * 1e3, "launches": len(mats)},
             "speedup_vs_loop": t_loop / t_graph}
+
+
+def bench_split_precision(sg, W, torch, n=8192, err_n=4096, reps=3):
+    """Split-precision FP64 emulation (BF16 digit slices on the tensor cores): effective
+    GFLOP/s at n^3 for 0, 1, 2 levels, and the max-norm error against the library's
+    plain FP64 classical result (normwise: / (||A||_inf max|B|)) for inputs
+    u * 2^round(N(0, sigma)) at err_n^3."""
+    out = {"workload": f"m=n=k={n} FP64 via BF16 slices, A,B,C uniform[-1,1]", "levels": {}}
+    A, B, C = W.uniform_device(n, n, 11), W.uniform_device(n, n, 12), W.uniform_device(n, n, 13)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for L in (0, 1, 2):
+        sg.gemm(A, B, C, levels=L, dtype="oz_bf16")
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            sg.gemm(A, B, C, levels=L, dtype="oz_bf16")
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        out["levels"][str(L)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3}
+    del A, B, C
+    errs = {}
+    for sigma in (0, 4, 10):
+        A = torch.from_numpy(W.scaled(err_n, err_n, 21, sigma)).cuda()
+        B = torch.from_numpy(W.scaled(err_n, err_n, 22, sigma)).cuda()
+        ref = torch.zeros((err_n, err_n), dtype=torch.float64, device="cuda")
+        sg.classical(A, B, ref)
+        den = float(torch.max(torch.sum(torch.abs(A), dim=1))) * float(torch.max(torch.abs(B)))
+        row = {}
+        for L in (0, 1, 2):
+            Cz = torch.zeros_like(ref)
+            sg.gemm(A, B, Cz, levels=L, dtype="oz_bf16")
+            torch.cuda.synchronize()
+            row[str(L)] = float(torch.max(torch.abs(Cz - ref))) / den
+        errs[str(sigma)] = row
+    out["error_vs_fp64_classical"] = {"n": err_n, "by_sigma_then_levels": errs}
+    return out
 
 
 def cpu_oracle_effective(n, levels, reps=1):
@@ -345,6 +383,9 @@ def main():
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(sg, W, torch)
+    split = None
+    if not args.no_split and rank == 0:
+        split = bench_split_precision(sg, W, torch)
 
     if rank != 0:
         if dist is not None:
@@ -376,6 +417,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
+        "split_precision": split,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }

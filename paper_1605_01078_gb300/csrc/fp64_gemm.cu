@@ -28,7 +28,8 @@
 // the FP64 pipe by two orders of magnitude over HBM.  The design therefore keeps the
 // FP64 pipe fed with nothing but the product's FMAs in the consumer warps (staging,
 // address arithmetic, operand sums and barrier traffic live in the producer warps),
-// forms each operand sum once per staged tile, uses sign-bit flips for negation, and
+// forms each operand sum once per staged tile with an integer-pipe binary64 addition
+// (int_fadd.h, bit-identical to DADD), uses sign-bit flips for negation, and
 // balances work across the 152 SMs exactly (stream-K ranges of the (unit, k-step)
 // space).  Atomic C updates (red.global.add.f64) execute in the L2, off the SM's FP64
 // pipe.
@@ -42,6 +43,7 @@
 #include <mutex>
 #include <vector>
 
+#include "int_fadd.h"
 #include "internal.h"
 
 namespace sgb {
@@ -373,10 +375,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
         if (k0 + kk < d.hk) {
           const int src = i * BK + kk;
           v = flip_sign(ra[src], term_neg(c_plans.ta[row][0]));
-          for (int t = 1; t < na; ++t) {
-            const double x = ra[t * BM * BK + src];
-            v = term_neg(c_plans.ta[row][t]) ? v - x : v + x;
-          }
+          for (int t = 1; t < na; ++t)  // integer-pipe addition, bit-identical to DADD
+            v = int_fadd(v, ra[t * BM * BK + src], term_neg(c_plans.ta[row][t]));
         }
         sa[e] = v;
       }
@@ -387,10 +387,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
         double v = 0.0;
         if (k0 + kk < d.hk) {
           v = flip_sign(rb[e], term_neg(c_plans.tb[row][0]));
-          for (int t = 1; t < nb; ++t) {
-            const double x = rb[t * BK * BN + e];
-            v = term_neg(c_plans.tb[row][t]) ? v - x : v + x;
-          }
+          for (int t = 1; t < nb; ++t)
+            v = int_fadd(v, rb[t * BK * BN + e], term_neg(c_plans.tb[row][t]));
         }
         sb[e] = v;
       }

@@ -37,6 +37,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "int_fadd.h"
 #include "internal.h"
 
 namespace sgb {
@@ -121,7 +122,7 @@ __device__ __forceinline__ double operand_sum(const double* src, int64_t ld, int
     double x = 0.0;
     if (r < h_r && c < h_c && gr < rows && gc < cols) x = src[gr * ld + gc];
     if (t == 0) v = term_neg(code) ? -x : x;
-    else v = term_neg(code) ? v - x : v + x;
+    else v = int_fadd(v, x, term_neg(code));  // integer pipe, bit-identical to DADD
   }
   return v;
 }

@@ -234,9 +234,41 @@ def load_rows(path: str):
         return json.load(fh)
 
 
+SWEEP_SQUARE = [2048 * i for i in range(1, 9)]
+SWEEP_RANKK = [256, 512, 1024, 2048, 4096]
+
+
+def sweep(out_dir: str) -> List[Dict]:
+    """The FP64 shape sweep: square m = n = k in 2048..16384 (step 2048) and rank-k
+    m = n = 16384 with k in 256..4096, every candidate, effective GFLOP/s (2mnk/t);
+    writes sweep_fp64.json and sweep_fp64.md into out_dir."""
+    import os
+    shapes = [(n, n, n) for n in SWEEP_SQUARE] + [(16384, 16384, k) for k in SWEEP_RANKK]
+    timer = Timer(16384 * 16384, 16384 * 16384, 16384 * 16384)
+    rows = []
+    for (m, n, k) in shapes:
+        row = measure([(m, n, k)], B.STRASSEN_F64, timer)[0]
+        rows.append(row)
+    names = ["classical", "1L ABC", "1L AB", "1L Naive", "2L ABC", "2L AB", "2L Naive"]
+    lines = ["| m | n | k | " + " | ".join(names) + " | best | best / classical |",
+             "|" + "---|" * (len(names) + 5)]
+    for r in rows:
+        eff = [2.0 * r["m"] * r["n"] * r["k"] / t / 1e9 for t in r["times"]]
+        b = best_of(r)
+        lines.append(f"| {r['m']} | {r['n']} | {r['k']} | " + " | ".join(f"{v:.0f}" for v in eff) +
+                     f" | {names[b]} | {eff[b] / eff[0]:.3f} |")
+    os.makedirs(out_dir, exist_ok=True)
+    save_rows(os.path.join(out_dir, "sweep_fp64.json"), rows)
+    with open(os.path.join(out_dir, "sweep_fp64.md"), "w") as fh:
+        fh.write("Effective GFLOP/s (2mnk/t), FP64, A, B, C uniform[-1,1], one GB300\n\n" + "\n".join(lines) + "\n")
+    print("\n".join(lines))
+    return rows
+
+
 def main(argv=None) -> int:
     """Exhaustive timing of seeded random shapes, selector training and held-out
-    evaluation; writes rows, parameters and a regret summary as JSON into --out."""
+    evaluation; writes rows, parameters and a regret summary as JSON into --out.
+    With --sweep, runs the FP64 shape sweep instead."""
     import argparse
     import os
     import sys
@@ -250,7 +282,11 @@ def main(argv=None) -> int:
     ap.add_argument("--hi", type=int, default=16384)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--out", required=True)
+    ap.add_argument("--sweep", action="store_true", help="run the FP64 shape sweep only")
     a = ap.parse_args(argv)
+    if a.sweep:
+        sweep(a.out)
+        return 0
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
         sys.path.insert(0, root)

@@ -94,3 +94,25 @@ def test_status_strings():
 def test_select_fixed_rule_without_model():
     lv, var, tile = sg.strassen_select(8192, 8192, 8192, 0)
     assert lv in (0, 1, 2) and var in (0, 1, 2) and tile >= 0
+
+
+def test_analytic_model_counts():
+    """The analytic model's arithmetic terms (Section 4.2's T_a restated for the GPU
+    tile): on tile-aligned sizes the products cost 7/8 (one level) and 49/64 (two
+    levels) of the classical multiply-adds, plus the staging additions."""
+    f = sg.strassen_model_seconds
+    n = 8192
+    t0 = f(n, n, n, 0, sg.STRASSEN_ABC)
+    fma_rate = 2.0 * 152 * 2.07e9
+    assert abs(t0 - (n ** 3 / fma_rate + 4e-6)) / t0 < 1e-9
+    t1 = f(n, n, n, 1, sg.STRASSEN_ABC)
+    t2 = f(n, n, n, 2, sg.STRASSEN_ABC)
+    # ABC one level: 7 products of (n/2)^3 FMAs, sums (na-1)/128 + (nb-1)/128 per FMA at 1.2 FMA each
+    fma1 = 7 * (n // 2) ** 3
+    adds1 = (n // 2) ** 3 * (5 + 5) / 128.0   # 5 extra A terms and 5 extra B terms over the 7 products
+    assert abs(t1 - ((fma1 + 1.2 * adds1) / fma_rate + 4e-6)) / t1 < 1e-9
+    assert t2 < t1 < t0
+    # Naive re-forms sums once: cheaper sums, extra memory passes and launches
+    assert f(n, n, n, 2, sg.STRASSEN_NAIVE) < t2
+    assert f(256, 256, 256, 2, sg.STRASSEN_NAIVE) > f(256, 256, 256, 0, sg.STRASSEN_ABC)
+    assert f(0, 4, 4, 1, 0) == -1.0
