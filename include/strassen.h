@@ -226,7 +226,11 @@ STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int 
  *                        on `count` parameters with moment buffers m, v (DEVICE).
  * strassen_selector_load copies a trained parameter vector (HOST) to the current device
  *                        and makes strassen_select() use it; strassen_selector_clear
- *                        forgets it.
+ *                        forgets it (and re-enables every dtype).
+ * strassen_selector_use  enables (1) or disables (0) the network for one dtype
+ *                        (default: all enabled); with it disabled, strassen_select()
+ *                        falls through to the analytic model for that dtype.  The tuning
+ *                        driver enables it only where it beat the model on held-out shapes.
  * All return STRASSEN_OK or a negative status; the kernels run on `stream`.
  */
 STRASSEN_API int strassen_mlp_param_count(void);
@@ -238,6 +242,7 @@ STRASSEN_API int strassen_mlp_loss_grad(const float* params, const float* X, con
 STRASSEN_API int strassen_mlp_adam(float* params, const float* grad, float* m, float* v, int count,
                                    int step, float lr, strassen_stream_t stream);
 STRASSEN_API int strassen_selector_load(const float* params_host, int count);
+STRASSEN_API int strassen_selector_use(int dtype, int enable);
 STRASSEN_API int strassen_selector_clear(void);
 
 /*
@@ -298,6 +303,17 @@ STRASSEN_API int strassen_device_status(strassen_stream_t stream);
  * negative status (STRASSEN_ERR_ARG for a negative limit).
  */
 STRASSEN_API int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stream_t stream);
+
+/*
+ * strassen_check_int_fadd -- diagnostic: on the current device, adds and subtracts
+ * `count` hashed pairs of doubles (arbitrary bit patterns, near-cancelling pairs,
+ * subnormals, wide exponent gaps) both with the hardware FP64 addition and with the
+ * integer-pipe addition the staging kernels use for operand sums, and stores in
+ * *mismatches (HOST pointer) how many results differ bitwise.  Synchronises `stream`.
+ * Returns STRASSEN_OK or a negative status.
+ */
+STRASSEN_API int strassen_check_int_fadd(int64_t count, uint64_t seed, uint64_t* mismatches,
+                                         strassen_stream_t stream);
 
 /* strassen_status_string -- a static, NUL-terminated description of a status code. */
 STRASSEN_API const char* strassen_status_string(int status);

@@ -22,7 +22,7 @@ from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  
                        strassen_check_wait_timeout, strassen_tune_record, strassen_tune_clear,
                        strassen_model_seconds, strassen_mlp_param_count, strassen_mlp_forward,
                        strassen_mlp_loss_grad, strassen_mlp_adam, strassen_selector_load,
-                       strassen_selector_clear,
+                       strassen_selector_clear, strassen_check_int_fadd, strassen_selector_use,
                        strassen_workspace_size)
 
 VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO}

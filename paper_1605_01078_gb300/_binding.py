@@ -61,8 +61,10 @@ SIGNATURES = {
     "strassen_mlp_loss_grad": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, _P, _P]),
     "strassen_mlp_adam": (_I, [_P, _P, _P, _P, _I, _I, ctypes.c_float, _P]),
     "strassen_selector_load": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
+    "strassen_selector_use": (_I, [_I, _I]),
     "strassen_selector_clear": (_I, []),
     "strassen_check_wait_timeout": (_I, [_I64, _P]),
+    "strassen_check_int_fadd": (_I, [_I64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),
 }
 
 
@@ -118,6 +120,14 @@ def strassen_check_wait_timeout(limit_cycles, stream) -> int:
     return lib().strassen_check_wait_timeout(limit_cycles, stream)
 
 
+def strassen_check_int_fadd(count, seed, stream=0) -> int:
+    """Number of hashed pairs where the library's integer-pipe addition differs from
+    the hardware FP64 addition on this device (raises on error)."""
+    mm = ctypes.c_uint64(0)
+    _check(lib().strassen_check_int_fadd(count, seed, ctypes.byref(mm), stream), "strassen_check_int_fadd")
+    return mm.value
+
+
 def strassen_select(m, n, k, dtype):
     lv, var, tile = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     st = lib().strassen_select(m, n, k, dtype, ctypes.byref(lv), ctypes.byref(var), ctypes.byref(tile))
@@ -155,6 +165,10 @@ def strassen_mlp_adam(params, grad, m, v, count, step, lr, stream) -> int:
 
 def strassen_selector_load(params_host, count) -> int:
     return lib().strassen_selector_load(params_host, count)
+
+
+def strassen_selector_use(dtype, enable) -> int:
+    return lib().strassen_selector_use(dtype, enable)
 
 
 def strassen_selector_clear() -> int:

@@ -267,6 +267,16 @@ int strassen_device_status(strassen_stream_t stream) {
   return a != STRASSEN_OK ? a : b;
 }
 
+int strassen_check_int_fadd(int64_t count, uint64_t seed, uint64_t* mismatches, strassen_stream_t stream) {
+  if (count < 0) return STRASSEN_ERR_ARG;
+  if (!mismatches) return STRASSEN_ERR_NULL;
+  unsigned long long mm = 0;
+  const cudaError_t e = check_int_fadd((long long)count, (unsigned long long)seed, &mm, (cudaStream_t)stream);
+  if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+  *mismatches = (uint64_t)mm;
+  return STRASSEN_OK;
+}
+
 int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stream_t stream) {
   if (limit_cycles < 0) return STRASSEN_ERR_ARG;
   return cuda_status(launch_wait_timeout_check((long long)limit_cycles, (cudaStream_t)stream));

@@ -754,6 +754,73 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
                           stream);
 }
 
+namespace {
+
+// Diagnostic: count pairs where the integer-pipe addition differs bitwise from the
+// hardware DADD.  Pairs come from a counter-based hash (splitmix64) of (seed, index),
+// mixing arbitrary bit patterns, moderate values and near-cancelling neighbours.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+
+__global__ void int_fadd_check_kernel(long long count, unsigned long long seed, unsigned long long* mismatches) {
+  unsigned long long local = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long r1 = splitmix64(seed ^ (2 * (unsigned long long)i));
+    const unsigned long long r2 = splitmix64(seed ^ (2 * (unsigned long long)i + 1));
+    double a, b;
+    switch (r1 & 3) {
+      case 0:  // arbitrary bit patterns
+        a = __longlong_as_double((long long)r1);
+        b = __longlong_as_double((long long)r2);
+        break;
+      case 1:  // neighbours: heavy cancellation
+        a = __longlong_as_double((long long)((r1 & 0x800fffffffffffffULL) | 0x3ff0000000000000ULL));
+        b = __longlong_as_double((long long)(((unsigned long long)__double_as_longlong(a) ^ (r2 & 0xfffULL)) ^
+                                             (r2 & 0x8000000000000000ULL)));
+        break;
+      case 2:  // subnormals and tiny normals
+        a = __longlong_as_double((long long)(r1 & 0x801fffffffffffffULL));
+        b = __longlong_as_double((long long)(r2 & 0x801fffffffffffffULL));
+        break;
+      default:  // moderate values with exponent gaps up to 70
+        a = scalbn((double)(r1 >> 11) * 0x1p-53, (int)(r2 % 60) - 30);
+        b = scalbn((double)(r2 >> 11) * 0x1p-53 * ((r1 >> 1) & 1 ? 1.0 : -1.0), (int)(r2 % 60) - 30 - (int)(r1 % 71));
+        break;
+    }
+    for (int neg = 0; neg < 2; ++neg) {
+      const double want = neg ? __dsub_rn(a, b) : __dadd_rn(a, b);
+      const double got = int_fadd(a, b, neg != 0);
+      const bool same = (want != want) ? (got != got) : (__double_as_longlong(want) == __double_as_longlong(got));
+      if (!same) ++local;
+    }
+  }
+  if (local) atomicAdd(mismatches, local);
+}
+
+}  // namespace
+
+cudaError_t check_int_fadd(long long count, unsigned long long seed, unsigned long long* mismatches_host,
+                           cudaStream_t stream) {
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMallocAsync(&d, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), stream);
+  if (e == cudaSuccess) {
+    int_fadd_check_kernel<<<std::max(device_sm_count(), 1) * 4, 256, 0, stream>>>(count, seed, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(mismatches_host, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream);
+  cudaFreeAsync(d, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  return e;
+}
+
 cudaError_t launch_wait_timeout_check(long long limit_cycles, cudaStream_t stream) {
   wait_timeout_check_kernel<<<1, 32, 0, stream>>>(limit_cycles);
   return cudaGetLastError();

@@ -80,6 +80,11 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
 // STRASSEN_ERR_TIMEOUT and the kernel returns).
 cudaError_t launch_wait_timeout_check(long long limit_cycles, cudaStream_t stream);
 
+// Counts, over `count` hashed pairs, where the integer-pipe addition (int_fadd.h)
+// differs bitwise from the hardware DADD on this device; synchronises `stream`.
+cudaError_t check_int_fadd(long long count, unsigned long long seed, unsigned long long* mismatches_host,
+                           cudaStream_t stream);
+
 // Picks a schedule for a launch (balance heuristics for the SM count).
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic);
 

@@ -149,6 +149,7 @@ float* g_sel_params = nullptr;  // device copy of the loaded network (device 0 o
 int* g_sel_out = nullptr;
 cudaStream_t g_sel_stream = nullptr;
 int g_sel_device = -1;
+unsigned g_sel_dtypes = 0x7u;  // bit d: use the network for dtype d
 
 int grid_for_batch(int batch) { return batch < 1 ? 1 : (batch < 1024 ? batch : 1024); }
 
@@ -165,7 +166,7 @@ void mlp_features(int64_t m, int64_t n, int64_t k, int dtype, float* x) {
 
 bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
-  if (!g_sel_params) return false;
+  if (!g_sel_params || dtype < 0 || dtype > 2 || !((g_sel_dtypes >> dtype) & 1u)) return false;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != g_sel_device) {
     cudaGetLastError();
@@ -245,6 +246,14 @@ int strassen_selector_load(const float* params_host, int count) {
   return STRASSEN_OK;
 }
 
+int strassen_selector_use(int dtype, int enable) {
+  if (dtype < 0 || dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_mlp_mu);
+  if (enable) g_sel_dtypes |= 1u << dtype;
+  else g_sel_dtypes &= ~(1u << dtype);
+  return STRASSEN_OK;
+}
+
 int strassen_selector_clear(void) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
   if (g_sel_params) {
@@ -257,6 +266,7 @@ int strassen_selector_clear(void) {
     g_sel_stream = nullptr;
     g_sel_device = -1;
   }
+  g_sel_dtypes = 0x7u;
   return STRASSEN_OK;
 }
 

@@ -224,6 +224,22 @@ def load_selector(params: np.ndarray) -> None:
         raise B.StrassenError(st, "strassen_selector_load")
 
 
+def load_default_selector() -> Dict:
+    """Load the network shipped with the package (trained on this library's timings on
+    a GB300) into the library, enabled for the dtypes where it beat the analytic model
+    on held-out shapes.  Returns the file's metadata."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "selector_gb300.json")
+    with open(path) as fh:
+        meta = json.load(fh)
+    load_selector(np.array(meta["params"], dtype=np.float32))
+    for d, on in meta["use_for_dtype"].items():
+        st = B.strassen_selector_use(int(d), 1 if on else 0)
+        if st != 0:
+            raise B.StrassenError(st, "strassen_selector_use")
+    return {k: v for k, v in meta.items() if k != "params"}
+
+
 def save_rows(path: str, rows) -> None:
     with open(path, "w") as fh:
         json.dump(rows, fh)

@@ -126,3 +126,10 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     torch.cuda.synchronize()
     assert np.array_equal(dC.cpu().numpy(), A @ B)
     assert sg.strassen_device_status(s) == 0
+
+
+def test_integer_pipe_addition_matches_dadd_on_the_device():
+    """The staging kernels form operand sums with an integer-pipe binary64 addition;
+    on the GPU it must agree bitwise with the hardware FP64 addition."""
+    assert sg.strassen_check_int_fadd(1 << 24, 12345) == 0
+    assert sg.strassen_check_int_fadd(1 << 20, 999) == 0

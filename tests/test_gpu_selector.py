@@ -38,3 +38,32 @@ def test_selector_on_live_timings():
             assert (lv, var) == tune.CANDIDATES[c]
     finally:
         sg.strassen_selector_clear()
+
+
+def test_selector_gain_on_split_precision():
+    """For the tensor-core (split-precision) dtype there is no analytic model; the
+    selection without the network is the fixed classical choice.  The trained network
+    must pick better on held-out shapes."""
+    train_shapes = W.loguniform_shapes(40, seed=13, lo=256, hi=4096)
+    held_shapes = W.loguniform_shapes(24, seed=14, lo=256, hi=4096)
+    timer = tune.Timer(4096 * 4096, 4096 * 4096, 4096 * 4096)
+    oz = sg.STRASSEN_F64_OZ_BF16
+    train_rows = tune.measure(train_shapes, oz, timer)
+    held_rows = tune.measure(held_shapes, oz, timer)
+    params, _ = tune.train(train_rows, steps=2000, lr=3e-3, seed=0)
+    r_mlp = tune.regret(held_rows, tune.choose_mlp(params, held_rows))
+    r_without = tune.regret(held_rows, tune.choose_fixed(held_rows, 0))
+    print("split precision: regret mlp", r_mlp, "without the network", r_without)
+    assert r_mlp["mean"] <= r_without["mean"]
+
+
+def test_shipped_selector_loads():
+    meta = tune.load_default_selector()
+    try:
+        assert meta["use_for_dtype"]["2"] is True
+        lv, var, _ = sg.strassen_select(8192, 8192, 8192, sg.STRASSEN_F64_OZ_BF16)
+        assert (lv, var) in [tune.CANDIDATES[c] for c in tune.VALID[sg.STRASSEN_F64_OZ_BF16]]
+        # FP64 stays with the analytic model (it beat the network on held-out shapes)
+        assert sg.strassen_select(8192, 8192, 8192, sg.STRASSEN_F64)[0] == 2
+    finally:
+        sg.strassen_selector_clear()
