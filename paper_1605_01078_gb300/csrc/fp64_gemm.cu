@@ -362,21 +362,23 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       const ProbDesc& d = desc_of<BATCHED>(a, cur.p);
       const int row = d.plan_row + cur.r;
       const int na = min((int)c_plans.na[row], MAXT), nb = min((int)c_plans.nb[row], MAXT);
-      const double* ra = rawA + slot * S::kRawA;
-      const double* rb = rawB + slot * S::kRawB;
-      double* sa = sumA + q * BK * BM;
-      double* sb = sumB + q * BK * BN;
+      // The sums run on binary64 bit patterns with the integer-pipe addition: no
+      // floating-point value (or instruction) appears in the producer's path.
+      const uint64_t* ra = reinterpret_cast<const uint64_t*>(rawA + slot * S::kRawA);
+      const uint64_t* rb = reinterpret_cast<const uint64_t*>(rawB + slot * S::kRawB);
+      uint64_t* sa = reinterpret_cast<uint64_t*>(sumA + q * BK * BM);
+      uint64_t* sb = reinterpret_cast<uint64_t*>(sumB + q * BK * BN);
       const int64_t k0 = (int64_t)cur.ks * BK;
 #pragma unroll
       for (int qq = 0; qq < (BM * BK) / kProducers; ++qq) {
         const int e = pt + qq * kProducers;
         const int kk = e / BM, i = e - (e / BM) * BM;
-        double v = 0.0;
+        uint64_t v = 0;
         if (k0 + kk < d.hk) {
           const int src = i * BK + kk;
-          v = flip_sign(ra[src], term_neg(c_plans.ta[row][0]));
-          for (int t = 1; t < na; ++t)  // integer-pipe addition, bit-identical to DADD
-            v = int_fadd(v, ra[t * BM * BK + src], term_neg(c_plans.ta[row][t]));
+          v = ra[src] ^ ((uint64_t)term_neg(c_plans.ta[row][0]) << 63);
+          for (int t = 1; t < na; ++t)
+            v = int_fadd_bits(v, ra[t * BM * BK + src] ^ ((uint64_t)term_neg(c_plans.ta[row][t]) << 63));
         }
         sa[e] = v;
       }
@@ -384,11 +386,11 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       for (int qq = 0; qq < (BN * BK) / kProducers; ++qq) {
         const int e = pt + qq * kProducers;
         const int kk = e / BN;
-        double v = 0.0;
+        uint64_t v = 0;
         if (k0 + kk < d.hk) {
-          v = flip_sign(rb[e], term_neg(c_plans.tb[row][0]));
+          v = rb[e] ^ ((uint64_t)term_neg(c_plans.tb[row][0]) << 63);
           for (int t = 1; t < nb; ++t)
-            v = int_fadd(v, rb[t * BK * BN + e], term_neg(c_plans.tb[row][t]));
+            v = int_fadd_bits(v, rb[t * BK * BN + e] ^ ((uint64_t)term_neg(c_plans.tb[row][t]) << 63));
         }
         sb[e] = v;
       }

@@ -43,7 +43,7 @@ __host__ __device__ __forceinline__ uint64_t ifa_shr_jam(uint64_t x, int n) {
 // Round s (value s * 2^(e - 1078): three extra low bits; the leading one at bit 55 for a
 // normal result, below it only when e == 1, i.e. a subnormal result) to nearest even
 // and pack it with `sign`.
-__host__ __device__ __forceinline__ double ifa_round_pack(uint64_t sign, int e, uint64_t s) {
+__host__ __device__ __forceinline__ uint64_t ifa_round_pack(uint64_t sign, int e, uint64_t s) {
   const uint64_t low = s & 7;
   uint64_t sig = s >> 3;
   if (low > 4 || (low == 4 && (sig & 1))) sig += 1;
@@ -51,26 +51,27 @@ __host__ __device__ __forceinline__ double ifa_round_pack(uint64_t sign, int e, 
     sig >>= 1;
     e += 1;
   }
-  if (e >= 2047) return ifa_double(sign | 0x7ff0000000000000ULL);  // overflow to infinity
-  if (sig < (1ULL << 52)) return ifa_double(sign | sig);             // subnormal: exponent field 0
-  return ifa_double(sign | ((uint64_t)e << 52) | (sig & ((1ULL << 52) - 1)));
+  if (e >= 2047) return sign | 0x7ff0000000000000ULL;  // overflow to infinity
+  if (sig < (1ULL << 52)) return sign | sig;             // subnormal: exponent field 0
+  return sign | ((uint64_t)e << 52) | (sig & ((1ULL << 52) - 1));
 }
 
-// a + b, or a - b when `negate_b`, rounded to nearest even.
-__host__ __device__ __forceinline__ double int_fadd(double a, double b, bool negate_b) {
-  uint64_t ua = ifa_bits(a), ub = ifa_bits(b) ^ (negate_b ? 0x8000000000000000ULL : 0);
+// The bits of a + b (b's sign bit already flipped for a subtraction), rounded to
+// nearest even; operands and result are binary64 bit patterns, so no value of floating
+// type (and no floating-point instruction) appears in the computation.
+__host__ __device__ __forceinline__ uint64_t int_fadd_bits(uint64_t ua, uint64_t ub) {
   const uint64_t kExpMask = 0x7ff0000000000000ULL, kMag = 0x7fffffffffffffffULL;
   // Infinities and NaNs: rare; follow the definition of IEEE addition.
   if ((ua & kExpMask) == kExpMask || (ub & kExpMask) == kExpMask) {
     const bool nan_a = (ua & kMag) > kExpMask, nan_b = (ub & kMag) > kExpMask;
-    if (nan_a || nan_b) return ifa_double(0x7ff8000000000000ULL);
+    if (nan_a || nan_b) return 0x7ff8000000000000ULL;
     const bool inf_a = (ua & kMag) == kExpMask, inf_b = (ub & kMag) == kExpMask;
-    if (inf_a && inf_b) return ((ua ^ ub) >> 63) ? ifa_double(0x7ff8000000000000ULL) : ifa_double(ua);
-    return inf_a ? ifa_double(ua) : ifa_double(ub);
+    if (inf_a && inf_b) return ((ua ^ ub) >> 63) ? 0x7ff8000000000000ULL : ua;
+    return inf_a ? ua : ub;
   }
   // Zeros: x + 0 = x; (+0) + (-0) = +0 and (-0) + (-0) = -0 under round to nearest.
-  if ((ub & kMag) == 0) return (ua & kMag) == 0 ? ifa_double(ua & ub) : ifa_double(ua);
-  if ((ua & kMag) == 0) return ifa_double(ub);
+  if ((ub & kMag) == 0) return (ua & kMag) == 0 ? (ua & ub) : ua;
+  if ((ua & kMag) == 0) return ub;
   // Order by magnitude: |a| >= |b|.
   if ((ub & kMag) > (ua & kMag)) {
     const uint64_t t = ua;
@@ -94,7 +95,7 @@ __host__ __device__ __forceinline__ double int_fadd(double a, double b, bool neg
     }
   } else {
     s = ma - mb;                       // >= 0 since |a| >= |b|
-    if (s == 0) return ifa_double(0);  // exact cancellation gives +0
+    if (s == 0) return 0;  // exact cancellation gives +0
     const int lz = ifa_clz64(s) - 8;   // the leading one belongs at bit 55
     if (lz > 0) {
       const int shift = lz < e - 1 ? lz : e - 1;  // never below the subnormal exponent
@@ -103,6 +104,11 @@ __host__ __device__ __forceinline__ double int_fadd(double a, double b, bool neg
     }
   }
   return ifa_round_pack(sign, e, s);
+}
+
+// a + b, or a - b when `negate_b`, rounded to nearest even.
+__host__ __device__ __forceinline__ double int_fadd(double a, double b, bool negate_b) {
+  return ifa_double(int_fadd_bits(ifa_bits(a), ifa_bits(b) ^ (negate_b ? 0x8000000000000000ULL : 0)));
 }
 
 }  // namespace sgb

@@ -70,8 +70,7 @@ __device__ __forceinline__ int scale_exponent(unsigned long long mag) {
 }
 
 // rint(x * 2^(56 - e)) as an integer, computed on the bits of x (|x| < 2^(e-1)).
-__device__ __forceinline__ long long scaled_rint(double x, int e) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+__device__ __forceinline__ long long scaled_rint(unsigned long long bits, int e) {
   const unsigned long long mag = bits & 0x7fffffffffffffffULL;
   if (mag == 0) return 0;
   int E = (int)(mag >> 52);
@@ -107,22 +106,24 @@ __device__ __forceinline__ void digits_of(long long N, float* d) {
   d[kS - 1] = (float)N;
 }
 
-__device__ __forceinline__ unsigned long long mag_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+__device__ __forceinline__ unsigned long long mag_bits(unsigned long long bits) {
+  return bits & 0x7fffffffffffffffULL;
 }
 
-// Operand sum x = sum_t sign_t * src[block_t](r, c), masked to the source extent.
-__device__ __forceinline__ double operand_sum(const double* src, int64_t ld, int64_t rows, int64_t cols,
-                                              int64_t h_r, int64_t h_c, const uint8_t* terms, int nterms,
-                                              int64_t r, int64_t c) {
-  double v = 0.0;
+// Bits of the operand sum x = sum_t sign_t * src[block_t](r, c), masked to the source
+// extent, formed with the integer-pipe addition (no floating-point instruction).
+__device__ __forceinline__ unsigned long long operand_sum(const double* src, int64_t ld, int64_t rows,
+                                                          int64_t cols, int64_t h_r, int64_t h_c,
+                                                          const uint8_t* terms, int nterms, int64_t r, int64_t c) {
+  const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
+  unsigned long long v = 0;
   for (int t = 0; t < nterms; ++t) {
     const uint8_t code = terms[t];
     const int64_t gr = (int64_t)term_bi(code) * h_r + r, gc = (int64_t)term_bj(code) * h_c + c;
-    double x = 0.0;
-    if (r < h_r && c < h_c && gr < rows && gc < cols) x = src[gr * ld + gc];
-    if (t == 0) v = term_neg(code) ? -x : x;
-    else v = int_fadd(v, x, term_neg(code));  // integer pipe, bit-identical to DADD
+    unsigned long long x = 0;
+    if (r < h_r && c < h_c && gr < rows && gc < cols) x = s64[gr * ld + gc];
+    x ^= (unsigned long long)term_neg(code) << 63;
+    v = t == 0 ? x : int_fadd_bits(v, x);
   }
   return v;
 }
@@ -142,7 +143,7 @@ struct SplitArgs {
 
 // One block per output row i of X^ (rows of A's operand sum), product blockIdx.y.
 __global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
-  extern __shared__ double rowbuf[];  // h_k doubles
+  extern __shared__ unsigned long long rowbuf[];  // h_k binary64 bit patterns
   __shared__ unsigned long long red[32];
   const int p = blockIdx.y;
   const int64_t i = blockIdx.x;
@@ -160,7 +161,7 @@ __global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
   }
   unsigned long long mx = 0;
   for (int64_t k = threadIdx.x; k < a.h_k; k += blockDim.x) {
-    const double x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, i, k);
+    const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, i, k);
     rowbuf[k] = x;
     mx = max(mx, mag_bits(x));
   }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ Spl
       float d[kS];
       long long N = 0;
       if (j < a.h_out && k < a.h_k) {
-        const double x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j);
+        const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j);
         N = scaled_rint(x, scale_exponent(colmax[0][cc]));
       }
       digits_of(N, d);

@@ -10,10 +10,11 @@
 //
 // The analytic model restates the paper's T = T_a + T_m for this GPU: T_a counts the
 // FP64 operations the kernels actually execute -- multiply-adds of the padded 128 x 128
-// x 8 tiles (the GPU's analogue of the m_R x n_R micro-tile), operand-sum additions
-// re-done for every tile (ABC, AB) or once (Naive), and C updates -- at the FP64 pipe
-// rate; T_m counts the extra passes of AB and Naive over their temporaries at the HBM
-// rate; and each kernel launch costs a fixed overhead.
+// x 8 tiles (the GPU's analogue of the m_R x n_R micro-tile), the operand-sum and C
+// additions of Naive and AB's separate kernels (the staging sums of ABC and AB run on
+// the integer pipe and cost no FP64 time) -- at the FP64 pipe rate; T_m counts the extra
+// passes of AB and Naive over their temporaries at the HBM rate; and each kernel launch
+// costs a fixed overhead.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,6 +29,7 @@ namespace {
 
 constexpr double kFmaPerSec = 2.0 * 152 * 2.07e9;   // FP64 pipe: 2 FMA / clk / SM
 constexpr double kAddCost = 1.2;                    // a DADD costs about 1.2 DFMA (measured)
+constexpr double kStageAddCost = 0.0;               // staging sums run on the integer pipe
 constexpr double kBytesPerSec = 6.8e12;             // HBM, measured copy bandwidth
 constexpr double kLaunchSec = 4e-6;
 constexpr int kBM = 128, kBN = 128, kBK = 8;
@@ -69,11 +71,12 @@ double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant) {
     fma = pm * pn * pk;
     launches = 1;
   } else if (variant == STRASSEN_ABC || variant == STRASSEN_AB) {
-    // Operand sums are re-formed for every tile: per product (na-1)/BN + (nb-1)/BM
-    // additions per multiply-add.
+    // Operand sums are re-formed for every tile, (na-1)/BN + (nb-1)/BM additions per
+    // multiply-add, but on the integer pipe of the producer warps (kStageAddCost).
     for (int r = 0; r < pl.nprod; ++r) {
       fma += pm * pn * pk;
-      adds += pm * pn * pk * ((pl.na[r] - 1) / (double)kBN + (pl.nb[r] - 1) / (double)kBM);
+      adds += kStageAddCost / kAddCost * pm * pn * pk *
+              ((pl.na[r] - 1) / (double)kBN + (pl.nb[r] - 1) / (double)kBM);
     }
     if (variant == STRASSEN_ABC) {
       launches = 1;
