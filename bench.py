@@ -8,7 +8,8 @@ larger than the 129 MB L2, so no flush is needed between steps).
 
 Metric: effective GFLOPS = 2mnk / t * 1e-9 (the paper's Eq. for effective GFLOPS).
 Also reported: the library's classical FP64 kernel on the same inputs (the
-comparator), an end-to-end figure with host buffers, the roofline of the FP64 product
+comparator), the same product with one and three levels, an end-to-end figure with
+host buffers, the roofline of the FP64 product
 kernel against the FP64 pipe, SM clocks sampled during the timed region, and the CPU
 oracle timed on a bounded sample.
 
@@ -57,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-levels", action="store_true", help="skip the other level counts (1 and 3 levels)")
     return ap.parse_args()
 
 
@@ -245,6 +247,28 @@ def bench_split_precision(sg, W, torch, n=8192, err_n=4096, reps=3):
     return out
 
 
+def bench_other_levels(sg, torch, A, B, C, stream, levels_list, variant="ABC", reps=3):
+    """The same product with other level counts (on the same resident inputs): effective
+    GFLOP/s and the FP64 pipe fraction of each, CUDA events per call."""
+    m, k = A.shape
+    n = B.shape[1]
+    out = {}
+    for lv in levels_list:
+        sg.gemm(A, B, C, levels=lv, variant=variant, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            sg.gemm(A, B, C, levels=lv, variant=variant, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        t = statistics.median(a.elapsed_time(b) / 1e3 for a, b in ev)
+        alg = algorithmic_flops(m, n, k, lv) / t / 1e9
+        out[str(lv)] = {"value": 2.0 * m * n * k / t / 1e9, "unit": UNIT, "ms": t * 1e3,
+                        "variant": variant, "algorithmic_gflops": alg, "frac": alg / FP64_PEAK_GFLOPS}
+    return out
+
+
 def cpu_oracle_effective(n, levels, reps=1):
     import numpy as np
     import oracle
@@ -399,6 +423,10 @@ def main():
                "h2d_bytes_per_step": int(3 * 8 * m * n), "d2h_bytes_per_step": int(8 * m * n)}
         del dA, dB, dC
 
+    levels_other = None
+    if not args.no_levels and args.dtype == "f64" and rank == 0:
+        levels_other = bench_other_levels(sg, torch, A, B, C, stream, [lv for lv in (1, 2, 3) if lv != L])
+
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(sg, W, torch)
@@ -454,6 +482,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "other_levels": levels_other,
         "batched": batched,
         "split_precision": split,
         "gpu_launches": launches_per_step * args.steps,

@@ -9,8 +9,9 @@
  *     row r of the L-level coefficient table,
  *         M_r = (sum_s delta_s X_s)(sum_t eps_t V_t);   C_q += gamma_q M_r,
  *     with X_s blocks of A, V_t blocks of B, C_q blocks of C in a 2^L x 2^L partition;
- *   - the one-level table of Figure 1 and the two-level table of Figure 2 (its
- *     Kronecker square);
+ *   - the one-level table of Figure 1, the two-level table of Figure 2 (its
+ *     Kronecker square) and the three-level table (its Kronecker cube: the
+ *     multi-level Strassen of Sections 3.5-3.6 one level further);
  *   - the three variants of Section 4.1: "ABC" (operand sums formed while operand
  *     tiles are staged, each M_r scattered into its C blocks in the kernel
  *     epilogue), "AB" (fused sums, explicit temporary M, separate C updates) and
@@ -81,7 +82,9 @@ typedef enum {
 #define STRASSEN_ERR_DIM (-1)         /* m, n or k negative */
 #define STRASSEN_ERR_LD (-2)          /* lda < k, ldb < n or ldc < n (with a non-empty operand) */
 #define STRASSEN_ERR_NULL (-3)        /* NULL pointer with a non-empty operand */
-#define STRASSEN_ERR_LEVELS (-4)      /* levels outside {-1, 0, 1, 2} */
+#define STRASSEN_ERR_LEVELS (-4)      /* levels outside {-1, 0, 1, 2, 3} */
+#define STRASSEN_MAX_LEVELS 3         /* deepest table built: 7^3 = 343 products */
+#define STRASSEN_MAX_TERMS 8          /* terms per operand / C targets per product (2^3) */
 #define STRASSEN_ERR_UNSUPPORTED (-5) /* unknown dtype or variant, or a combination not built */
 #define STRASSEN_ERR_CUDA (-6)        /* a CUDA runtime error */
 #define STRASSEN_ERR_TIMEOUT (-7)     /* a device-side wait gave up (batched work queue) */
@@ -93,9 +96,9 @@ typedef enum {
 /*
  * strassen_gemm -- C += A*B with `levels` levels of Strassen in `variant`.
  *
- * Defined by Eq. 4 (Section 3.6) with the Figure 1 table (levels = 1) or its
- * Kronecker square, Figure 2 (levels = 2); levels = 0 is the classical product of
- * Section 2.1.  levels = -1 or variant = STRASSEN_AUTO asks strassen_select() for the
+ * Defined by Eq. 4 (Section 3.6) with the Figure 1 table (levels = 1), its
+ * Kronecker square, Figure 2 (levels = 2), or its Kronecker cube (levels = 3, 343
+ * products); levels = 0 is the classical product of Section 2.1.  levels = -1 or variant = STRASSEN_AUTO asks strassen_select() for the
  * choice.  Levels are clamped down while 2^levels exceeds min(m, n, k) (a block would
  * be empty in every product); the call still succeeds.
  *
@@ -103,7 +106,7 @@ typedef enum {
  *   A, lda        device pointer and row stride (elements) of A, lda >= max(k, 1).
  *   B, ldb        device pointer and row stride of B, ldb >= max(n, 1).
  *   C, ldc        device pointer and row stride of C, ldc >= max(n, 1); read and written.
- *   levels        -1 (auto), 0, 1 or 2.
+ *   levels        -1 (auto), 0, 1, 2 or 3.
  *   variant       STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE or STRASSEN_AUTO.
  *   dtype         STRASSEN_F64 or one of the split-precision dtypes.
  *   stream        the CUDA stream the work is ordered on.
@@ -142,7 +145,7 @@ typedef struct {
   const double* B;
   double* C;
   int64_t lda, ldb, ldc;
-  int levels;               /* -1 = the autotuner's choice, else 0, 1 or 2 */
+  int levels;               /* -1 = the autotuner's choice, else 0, 1, 2 or 3 */
   strassen_variant variant; /* STRASSEN_AUTO = the autotuner's choice; AB and Naive run as ABC */
 } strassen_problem;
 
@@ -155,7 +158,7 @@ typedef struct {
  *           The byte ranges [C, C + (m-1)*ldc + n) of different problems must not
  *           overlap (STRASSEN_ERR_ARG otherwise).  levels = -1 or variant =
  *           STRASSEN_AUTO takes strassen_select()'s level; every problem runs as ABC
- *           (levels 1, 2) or classical (levels 0) inside the one launch.
+ *           (levels 1-3) or classical (levels 0) inside the one launch.
  *   dtype   STRASSEN_F64.
  *   stream  the CUDA stream.
  *
@@ -255,7 +258,7 @@ STRASSEN_API int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, in
                                 strassen_variant variant, strassen_dtype dtype);
 
 /*
- * strassen_gemm_ab_noalloc -- the AB variant (levels 1 or 2) that allocates nothing.
+ * strassen_gemm_ab_noalloc -- the AB variant (levels 1 to 3) that allocates nothing.
  * The paper has no counterpart: it is an interface for callers that cannot allocate
  * device memory while they run -- a process whose device memory is already claimed by
  * its own pooling allocator, a latency-bound loop where an allocation or a free may
@@ -270,7 +273,7 @@ STRASSEN_API int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, in
  *
  *   Limit:   ceil(m/2^L) * ceil(n/2^L) <= 4194304 (e.g. m = n = 4096 at one level,
  *            8192 at two); larger products return STRASSEN_ERR_SCRATCH_LIMIT and touch
- *            nothing.  levels outside {1, 2} return STRASSEN_ERR_LEVELS (levels are
+ *            nothing.  levels outside {1, 2, 3} return STRASSEN_ERR_LEVELS (levels are
  *            clamped as in strassen_gemm; a clamp to 0 runs classical_gemm).
  *   Set-up:  the first call on each device looks up the array's device address with
  *            cudaGetSymbolAddress while that device is current; make that first call
@@ -320,13 +323,14 @@ STRASSEN_API const char* strassen_status_string(int status);
 
 /*
  * strassen_plan_table -- copies the coefficient table the library uses for `levels`
- * (0, 1 or 2) into host arrays, for inspection and tests; no GPU work.
+ * (0 to STRASSEN_MAX_LEVELS) into host arrays, for inspection and tests; no GPU work.
  *
  * Each of the 7^levels products r has up to 2^levels terms per operand.  Term t of
- * product r is stored at index r*4 + t of a_terms, b_terms, c_terms as
- * (block_row * 16 + block_col) * 2 + (sign < 0), and the term counts at na[r], nb[r],
- * nc[r].  `capacity` is the number of products the arrays can hold (a_terms etc.
- * hold 4*capacity ints).  Returns the number of products, or a negative status.
+ * product r is stored at index r*STRASSEN_MAX_TERMS + t of a_terms, b_terms, c_terms
+ * as (block_row * 16 + block_col) * 2 + (sign < 0) (unused entries -1), and the term
+ * counts at na[r], nb[r], nc[r].  `capacity` is the number of products the arrays can
+ * hold (a_terms etc. hold STRASSEN_MAX_TERMS*capacity ints).  Returns the number of
+ * products, or a negative status.
  */
 STRASSEN_API int strassen_plan_table(int levels, int capacity, int* na, int* nb, int* nc,
                         int* a_terms, int* b_terms, int* c_terms);

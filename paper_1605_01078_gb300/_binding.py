@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libstrassen_gb300.so")
 # enums of strassen.h
 STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE, STRASSEN_AUTO = 0, 1, 2, 3
 STRASSEN_F64, STRASSEN_F64_OZ_INT8, STRASSEN_F64_OZ_BF16 = 0, 1, 2
+MAX_LEVELS, MAX_TERMS = 3, 8   # STRASSEN_MAX_LEVELS, STRASSEN_MAX_TERMS
 
 STATUS = {
     0: "STRASSEN_OK", -1: "STRASSEN_ERR_DIM", -2: "STRASSEN_ERR_LD", -3: "STRASSEN_ERR_NULL",
@@ -186,8 +187,8 @@ def strassen_status_string(status: int) -> str:
 def strassen_plan_table(levels: int):
     """The library's coefficient table for ``levels`` as a list of products, each a
     triple (a_terms, b_terms, c_terms) of (block_row, block_col, sign) tuples."""
-    cap = 49
-    arrs = [(ctypes.c_int * cap)() for _ in range(3)] + [(ctypes.c_int * (4 * cap))() for _ in range(3)]
+    cap, w = 343, MAX_TERMS
+    arrs = [(ctypes.c_int * cap)() for _ in range(3)] + [(ctypes.c_int * (w * cap))() for _ in range(3)]
     n = lib().strassen_plan_table(levels, cap, *arrs)
     if n < 0:
         raise StrassenError(n, "strassen_plan_table")
@@ -198,7 +199,7 @@ def strassen_plan_table(levels: int):
 
     out = []
     for r in range(n):
-        out.append((tuple(dec(ta[r * 4 + t]) for t in range(na[r])),
-                    tuple(dec(tb[r * 4 + t]) for t in range(nb[r])),
-                    tuple(dec(tc[r * 4 + t]) for t in range(nc[r]))))
+        out.append((tuple(dec(ta[r * w + t]) for t in range(na[r])),
+                    tuple(dec(tb[r * w + t]) for t in range(nb[r])),
+                    tuple(dec(tc[r * w + t]) for t in range(nc[r]))))
     return out

@@ -52,7 +52,7 @@ using namespace sgb;
 extern "C" int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                                         const double* B, int64_t ldb, double* C, int64_t ldc, int levels,
                                         strassen_stream_t stream) {
-  if (levels < 1 || levels > 2) return STRASSEN_ERR_LEVELS;
+  if (levels < 1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if (m == 0 || n == 0 || k == 0) return STRASSEN_OK;
   if (!A || !B || !C) return STRASSEN_ERR_NULL;

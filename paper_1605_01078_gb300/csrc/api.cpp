@@ -158,7 +158,7 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                   int64_t ldb, double* C, int64_t ldc, int levels, strassen_variant variant,
                   strassen_dtype dtype, strassen_stream_t stream) {
   try {
-    if (levels < -1 || levels > 2) return STRASSEN_ERR_LEVELS;
+    if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
     if ((int)variant < 0 || (int)variant > 3) return STRASSEN_ERR_UNSUPPORTED;
     if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
     const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
@@ -221,7 +221,7 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
     launches.reserve(count);
     for (int i = 0; i < count; ++i) {
       const strassen_problem& p = probs[i];
-      if (p.levels < -1 || p.levels > 2) return STRASSEN_ERR_LEVELS;
+      if (p.levels < -1 || p.levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
       if ((int)p.variant < 0 || (int)p.variant > 3) return STRASSEN_ERR_UNSUPPORTED;
       const int chk = check_args(p.m, p.n, p.k, p.A, p.lda, p.B, p.ldb, p.C, p.ldc);
       if (chk < 0) return chk;
@@ -316,7 +316,7 @@ int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* 
 int strassen_tune_record(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int levels,
                          strassen_variant variant, int tile_id) {
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
-  if (levels < 0 || levels > 2) return STRASSEN_ERR_LEVELS;
+  if (levels < 0 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
   if ((int)dtype < 0 || (int)dtype > 2 || (int)variant < 0 || (int)variant > 2) return STRASSEN_ERR_UNSUPPORTED;
   if (tile_id != 0) return STRASSEN_ERR_ARG;
   record_store(m, n, k, (int)dtype, levels, (int)variant, tile_id);
@@ -329,14 +329,14 @@ int strassen_tune_clear(void) {
 }
 
 double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant) {
-  if (m <= 0 || n <= 0 || k <= 0 || levels < 0 || levels > 2 || (int)variant < 0 || (int)variant > 2) return -1.0;
+  if (m <= 0 || n <= 0 || k <= 0 || levels < 0 || levels > kMaxLevels || (int)variant < 0 || (int)variant > 2) return -1.0;
   return model_seconds(m, n, k, levels, (int)variant);
 }
 
 int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant,
                                 strassen_dtype dtype) {
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
-  if (levels < -1 || levels > 2) return STRASSEN_ERR_LEVELS;
+  if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
   if ((int)variant < 0 || (int)variant > 3 || (int)dtype < 0 || (int)dtype > 2)
     return STRASSEN_ERR_UNSUPPORTED;
   if (m == 0 || n == 0 || k == 0) return 0;
@@ -382,10 +382,10 @@ int strassen_plan_table(int levels, int capacity, int* na, int* nb, int* nc, int
   auto enc = [](uint8_t c) { return (term_bi(c) * 16 + term_bj(c)) * 2 + term_neg(c); };
   for (int r = 0; r < pl.nprod; ++r) {
     na[r] = pl.na[r]; nb[r] = pl.nb[r]; nc[r] = pl.nc[r];
-    for (int t = 0; t < 4; ++t) {
-      a_terms[r * 4 + t] = t < pl.na[r] ? enc(pl.ta[r][t]) : -1;
-      b_terms[r * 4 + t] = t < pl.nb[r] ? enc(pl.tb[r][t]) : -1;
-      c_terms[r * 4 + t] = t < pl.nc[r] ? enc(pl.tc[r][t]) : -1;
+    for (int t = 0; t < kMaxTerms; ++t) {
+      a_terms[r * kMaxTerms + t] = t < pl.na[r] ? enc(pl.ta[r][t]) : -1;
+      b_terms[r * kMaxTerms + t] = t < pl.nb[r] ? enc(pl.tb[r][t]) : -1;
+      c_terms[r * kMaxTerms + t] = t < pl.nc[r] ? enc(pl.tc[r][t]) : -1;
     }
   }
   return pl.nprod;

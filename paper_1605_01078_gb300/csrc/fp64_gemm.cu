@@ -56,8 +56,14 @@ constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
 constexpr int kConsumers = 256;  // 8 warps: 16 x 16 threads, 8 x 8 outputs each
 constexpr int kProducers = 128;  // 4 warps: staging and operand sums
 constexpr int kThreads = kConsumers + kProducers;
-constexpr int NR = 2;  // ring of raw source tiles
 constexpr int NS = 4;  // ring of summed tiles
+// Ring of raw source tiles: two slots (the load of the next k-step overlaps the sums of
+// this one) while MAXT source tiles per operand fit twice in shared memory; one slot
+// for the eight-term products of three levels.  One k-step of the consumers takes
+// about 64K clocks of FP64 work per SM, so a producer that loads (about 1 us) and then
+// sums (a few us) each step still runs ahead of them through the summed ring.
+template <int MAXT>
+constexpr int raw_slots() { return MAXT >= 8 ? 1 : 2; }
 constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 // Register split (setmaxnreg): the block is launched with kLaunchRegs per thread;
 // the producer warpgroup gives registers back and the two consumer warpgroups take
@@ -94,11 +100,13 @@ struct KArgs {
 
 template <int MAXT>
 struct Smem {
+  static constexpr int NR = raw_slots<MAXT>();
   static constexpr int kRawA = MAXT * BM * BK;  // doubles per ring slot
   static constexpr int kRawB = MAXT * BK * BN;
   static constexpr size_t kBytes =
       sizeof(double) * (size_t)(NR * (kRawA + kRawB) + NS * BK * (BM + BN) + (kConsumers / 32) * 2 * BN) +
       sizeof(uint64_t) * (2 * NR + 2 * NS);
+  static_assert(kBytes <= 227 * 1024, "shared memory per block");
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -235,6 +243,7 @@ __device__ __forceinline__ void cursor_next(const KArgs& a, Cursor& c) {
 template <int MAXT, bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid_constant__ KArgs a) {
   using S = Smem<MAXT>;
+  constexpr int NR = S::NR;
   extern __shared__ __align__(128) double smem[];
   double* rawA = smem;                    // [NR][MAXT][BM][BK]   (TMA box layout: row, k)
   double* rawB = rawA + NR * S::kRawA;    // [NR][MAXT][BK][BN]
@@ -331,14 +340,19 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       }
     };
 
-    issue(cl, 0);
-    cursor_next<BATCHED>(a, cl);
-    int64_t issued = 1, landed = 0;
+    // Loads run NR - 1 steps ahead of the sums: step s + NR - 1 is issued into the
+    // slot that step s - 1 has released.
+    constexpr int kAhead = NR - 1;
+    int64_t issued = 0, landed = 0;
+    for (; issued < kAhead && issued < count; ++issued) {
+      issue(cl, (int)issued);
+      cursor_next<BATCHED>(a, cl);
+    }
     bool timed_out = false;
     for (int64_t s = 0; s < count && !timed_out; ++s) {
-      if (s + 1 < count) {
-        const int slot1 = (int)((s + 1) % NR);
-        const int64_t use1 = (s + 1) / NR;
+      if (s + kAhead < count) {
+        const int slot1 = (int)((s + kAhead) % NR);
+        const int64_t use1 = (s + kAhead) / NR;
         if (use1 > 0 && !mbar_wait(&raw_empty[slot1], (uint32_t)((use1 - 1) & 1))) {
           timed_out = true;
           break;
@@ -526,12 +540,28 @@ const void* kernel_fn() {
   return (const void*)fp64_strassen_kernel<MAXT, BATCHED>;
 }
 
+// Kernel instance by the largest term count of the launch's products: class c holds up
+// to 2^c source tiles per operand (c = 0..3).
+constexpr int kTermClasses = kMaxLevels + 1;
+template <bool BATCHED>
+const void* pick_kernel_b(int maxt_class) {
+  switch (maxt_class) {
+    case 0: return kernel_fn<1, BATCHED>();
+    case 1: return kernel_fn<2, BATCHED>();
+    case 2: return kernel_fn<4, BATCHED>();
+    default: return kernel_fn<8, BATCHED>();
+  }
+}
 const void* pick_kernel(int maxt_class, bool batched) {
-  if (batched) return maxt_class == 0 ? kernel_fn<1, true>() : maxt_class == 1 ? kernel_fn<2, true>() : kernel_fn<4, true>();
-  return maxt_class == 0 ? kernel_fn<1, false>() : maxt_class == 1 ? kernel_fn<2, false>() : kernel_fn<4, false>();
+  return batched ? pick_kernel_b<true>(maxt_class) : pick_kernel_b<false>(maxt_class);
 }
 size_t smem_bytes(int maxt_class) {
-  return maxt_class == 0 ? Smem<1>::kBytes : maxt_class == 1 ? Smem<2>::kBytes : Smem<4>::kBytes;
+  switch (maxt_class) {
+    case 0: return Smem<1>::kBytes;
+    case 1: return Smem<2>::kBytes;
+    case 2: return Smem<4>::kBytes;
+    default: return Smem<8>::kBytes;
+  }
 }
 
 cudaError_t ensure_device(int* sms_out) {
@@ -544,7 +574,7 @@ cudaError_t ensure_device(int* sms_out) {
   if (!st.ready) {
     st.ready = true;
     st.err = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int c = 0; c < 3 && st.err == cudaSuccess; ++c)
+    for (int c = 0; c < kTermClasses && st.err == cudaSuccess; ++c)
       for (int b = 0; b < 2 && st.err == cudaSuccess; ++b)
         st.err = cudaFuncSetAttribute(pick_kernel(c, b != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_bytes(c));
@@ -569,7 +599,7 @@ int term_class_of(int levels, int prod_begin, int nprod) {
     const int row = kPlanOffset[levels] + r;
     mx = std::max(mx, (int)std::max(kPlanTables.na[row], kPlanTables.nb[row]));
   }
-  return mx <= 1 ? 0 : (mx <= 2 ? 1 : 2);
+  return mx <= 1 ? 0 : (mx <= 2 ? 1 : (mx <= 4 ? 2 : 3));
 }
 
 bool encode_2d(CUtensorMap* map, const double* base, int64_t rows, int64_t cols, int64_t ld, int box_cols,
@@ -648,7 +678,7 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream) {
   int sms = 0;
   cudaError_t e = ensure_device(&sms);
   if (e != cudaSuccess) return e;
-  if (L.levels < 0 || L.levels > 2) return cudaErrorInvalidValue;
+  if (L.levels < 0 || L.levels > kMaxLevels) return cudaErrorInvalidValue;
   KArgs args;
   std::memset(&args, 0, sizeof(args));
   fill_desc(L, &args.single);

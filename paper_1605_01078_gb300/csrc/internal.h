@@ -9,7 +9,7 @@
 
 namespace sgb {
 
-constexpr int kMaxProducts = 49;
+constexpr int kMaxProducts = 343;
 
 // Host copy of the table of one level count (rows of kPlanTables).
 struct Plan {
@@ -19,7 +19,7 @@ struct Plan {
   uint8_t ta[kMaxProducts][kMaxTerms], tb[kMaxProducts][kMaxTerms], tc[kMaxProducts][kMaxTerms];
 };
 
-// Copies the table for levels 0, 1 or 2 (Figure 1 and its Kronecker square).
+// Copies the table for levels 0..kMaxLevels (Figure 1 and its Kronecker powers).
 // Returns false for other levels.
 bool make_plan(int levels, Plan* out);
 

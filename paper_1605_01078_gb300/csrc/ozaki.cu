@@ -503,6 +503,7 @@ struct RecombineArgs {
   int64_t ldc, m, n;
   int64_t hm, hn, h_mp, h_np;
   int levels, P;
+  int plan_off;   // table row of product 0 of the level
   const long long* t_hi;
   const long long* t_lo;
   const int* e;   // [P][h_mp]
@@ -572,7 +573,7 @@ __global__ void oz_recombine_scatter(const __grid_constant__ RecombineArgs a) {
   const int Pn = 1 << a.levels;
   const int64_t per_block = a.hm * a.hn;
   const int64_t total = per_block * Pn * Pn;
-  const int off = a.levels == 0 ? 0 : (a.levels == 1 ? 1 : 8);  // first table row of the level
+  const int off = a.plan_off;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(idx / per_block);
@@ -711,7 +712,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   RecombineArgs ra;
   ra.C = C; ra.ldc = ldc; ra.m = m; ra.n = n;
   ra.hm = hm; ra.hn = hn; ra.h_mp = hmp; ra.h_np = hnp;
-  ra.levels = levels; ra.P = P;
+  ra.levels = levels; ra.P = P; ra.plan_off = kPlanOffset[levels];
   ra.t_hi = thi; ra.t_lo = tlo; ra.e = ex; ra.f = fx;
   const int64_t total = hm * hn * (1LL << (2 * levels));
   const int threads = 256;

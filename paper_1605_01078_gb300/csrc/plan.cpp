@@ -6,7 +6,7 @@
 namespace sgb {
 
 bool make_plan(int levels, Plan* p) {
-  if (levels < 0 || levels > 2 || !p) return false;
+  if (levels < 0 || levels > kMaxLevels || !p) return false;
   std::memset(p, 0, sizeof(*p));
   p->levels = levels;
   p->nprod = kPlanCount[levels];

@@ -1,11 +1,13 @@
 // Coefficient tables of the general operation (Eq. 1, Eq. 3, Eq. 4), built at compile
 // time so that host code and device constant memory hold the same table.
 //
-// One level is Figure 1 (Section 3.1).  Two levels is its Kronecker square (Section
-// 3.5): product r = 7a + b applies outer product a to inner product b; along each
-// dimension the block index is 2 * outer + inner and signs multiply.  Figure 2 prints
-// this table with the C-update signs; its operand signs are printed as "+" throughout
-// and are not used.  Level 0 is the single classical product C00 += A00 B00.
+// One level is Figure 1 (Section 3.1).  L levels is its L-th Kronecker power
+// (Sections 3.5-3.6): product r = 7a + b of level L applies product a of level L - 1
+// (outer) to product b of Figure 1 (inner); along each dimension the block index is
+// 2 * outer + inner and signs multiply.  Figure 2 prints the two-level table with the
+// C-update signs; its operand signs are printed as "+" throughout and are not used.
+// Level 0 is the single classical product C00 += A00 B00.  Three levels (343 products
+// with up to 8 terms per operand and 8 C targets) is the deepest table built.
 #pragma once
 
 #include <stdint.h>
@@ -21,10 +23,11 @@ __host__ __device__ constexpr int term_bj(uint8_t c) { return c & 7; }
 __host__ __device__ constexpr int term_bi(uint8_t c) { return (c >> 3) & 7; }
 __host__ __device__ constexpr int term_neg(uint8_t c) { return (c >> 7) & 1; }
 
-constexpr int kMaxTerms = 4;
-constexpr int kTableRows = 1 + 7 + 49;
-constexpr int kPlanOffset[3] = {0, 1, 8};
-constexpr int kPlanCount[3] = {1, 7, 49};
+constexpr int kMaxLevels = 3;
+constexpr int kMaxTerms = 1 << kMaxLevels;
+constexpr int kTableRows = 1 + 7 + 49 + 343;
+constexpr int kPlanOffset[kMaxLevels + 1] = {0, 1, 8, 57};
+constexpr int kPlanCount[kMaxLevels + 1] = {1, 7, 49, 343};
 
 struct PlanTables {
   uint8_t na[kTableRows], nb[kTableRows], nc[kTableRows];
@@ -71,7 +74,7 @@ constexpr PlanTables build_tables() {
   PlanTables t{};
   t.na[0] = t.nb[0] = t.nc[0] = 1;
   t.ta[0][0] = t.tb[0][0] = t.tc[0][0] = term_code(0, 0, 0);
-  for (int L = 1; L <= 2; ++L) {
+  for (int L = 1; L <= kMaxLevels; ++L) {
     const int po = kPlanOffset[L - 1], pc = kPlanCount[L - 1], off = kPlanOffset[L];
     for (int a = 0; a < pc; ++a)
       for (int b = 0; b < 7; ++b) {

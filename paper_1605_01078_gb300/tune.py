@@ -256,7 +256,8 @@ SWEEP_RANKK = [256, 512, 1024, 2048, 4096]
 
 def sweep(out_dir: str) -> List[Dict]:
     """The FP64 shape sweep: square m = n = k in 2048..16384 (step 2048) and rank-k
-    m = n = 16384 with k in 256..4096, every candidate, effective GFLOP/s (2mnk/t);
+    m = n = 16384 with k in 256..4096, every candidate plus three-level ABC, effective
+    GFLOP/s (2mnk/t);
     writes sweep_fp64.json and sweep_fp64.md into out_dir."""
     import os
     shapes = [(n, n, n) for n in SWEEP_SQUARE] + [(16384, 16384, k) for k in SWEEP_RANKK]
@@ -264,13 +265,16 @@ def sweep(out_dir: str) -> List[Dict]:
     rows = []
     for (m, n, k) in shapes:
         row = measure([(m, n, k)], B.STRASSEN_F64, timer)[0]
+        # three levels (outside the selector's candidate set): ABC only
+        row["three_level_abc"] = timer.time(m, n, k, 3, B.STRASSEN_ABC, B.STRASSEN_F64)
         rows.append(row)
-    names = ["classical", "1L ABC", "1L AB", "1L Naive", "2L ABC", "2L AB", "2L Naive"]
+    names = ["classical", "1L ABC", "1L AB", "1L Naive", "2L ABC", "2L AB", "2L Naive", "3L ABC"]
     lines = ["| m | n | k | " + " | ".join(names) + " | best | best / classical |",
              "|" + "---|" * (len(names) + 5)]
     for r in rows:
-        eff = [2.0 * r["m"] * r["n"] * r["k"] / t / 1e9 for t in r["times"]]
-        b = best_of(r)
+        times = list(r["times"]) + [r["three_level_abc"]]
+        eff = [2.0 * r["m"] * r["n"] * r["k"] / t / 1e9 for t in times]
+        b = int(np.nanargmin(np.array(times, dtype=np.float64)))
         lines.append(f"| {r['m']} | {r['n']} | {r['k']} | " + " | ".join(f"{v:.0f}" for v in eff) +
                      f" | {names[b]} | {eff[b] / eff[0]:.3f} |")
     os.makedirs(out_dir, exist_ok=True)

@@ -37,14 +37,14 @@ def test_library_exports_every_declared_symbol():
         assert name in _binding.SIGNATURES, f"binding lacks {name}"
 
 
-@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
 def test_plan_table_matches_oracle_tables(levels):
     assert sg.strassen_plan_table(levels) == tables.table(levels)
 
 
 def test_plan_table_rejects_levels():
     with pytest.raises(sg.StrassenError):
-        sg.strassen_plan_table(3)
+        sg.strassen_plan_table(4)
 
 
 P = 0x1000  # a non-null dummy pointer: these calls must fail before touching it
@@ -69,7 +69,7 @@ def test_argument_checks(args, status):
 
 def test_levels_and_enums_checked():
     a = (4, 4, 4, P, 4, 2 * P, 4, 3 * P, 4)
-    assert sg.strassen_gemm(*a, 3, 0, 0, 0) == -4
+    assert sg.strassen_gemm(*a, 4, 0, 0, 0) == -4
     assert sg.strassen_gemm(*a, -2, 0, 0, 0) == -4
     assert sg.strassen_gemm(*a, 1, 7, 0, 0) == -5
     assert sg.strassen_gemm(*a, 1, 0, 9, 0) == -5

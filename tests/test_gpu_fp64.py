@@ -1,11 +1,11 @@
-"""GPU parity of the FP64 path (classical, 1/2-level ABC, AB, Naive) against the CPU
+"""GPU parity of the FP64 path (classical, 1/2/3-level ABC, AB, Naive) against the CPU
 oracle, through the C ABI.
 
 * Integer-valued inputs: every sum and product is exact in FP64, so the GPU result must
   equal the oracle bit for bit, for every variant, level and ragged shape.
 * Uniform[-1, 1] inputs, three checks:
   - normwise: max|C - C_ref| / (||A||_inf * max|B|) <= 1e-13 (classical, one level) or
-    1e-12 (two levels), C_ref from the oracle's classical definition (or its
+    1e-12 (two and three levels), C_ref from the oracle's classical definition (or its
     Dot2-compensated entries at full benchmark size).  ||A||_inf * max|B| bounds
     max|A B|, so this is the max-norm error relative to the size of the product;
   - classical: every entry within the rounding bound gamma_{k+1} (|C0| + |A||B|) of the
@@ -28,7 +28,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 VARIANTS = ["ABC", "AB", "NAIVE"]
-TOL = {0: 1e-13, 1: 1e-13, 2: 1e-12}
+TOL = {0: 1e-13, 1: 1e-13, 2: 1e-12, 3: 1e-12}
 U = 2.0 ** -53
 
 
@@ -56,7 +56,7 @@ def float_case(m, n, k, sa, sb, sc, zero_c):
     ref = ref_gemm(A, B, C)
     exact = exact_full(A, B, C)
     textbook = {}
-    for L in (1, 2):
+    for L in (1, 2, 3):
         t = np.array(C, copy=True)
         oracle.strassen(A, B, t, L)
         textbook[L] = float(np.max(np.abs(t - exact)))
@@ -103,7 +103,7 @@ SHAPES_INT = [(16, 16, 16), (1, 1, 1), (2, 3, 5), (13, 7, 11), (130, 257, 129), 
 
 
 @pytest.mark.parametrize("m,n,k", SHAPES_INT)
-@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_integer_bit_exact(m, n, k, levels, variant):
     A, B, C = W.integer(m, k, 1), W.integer(k, n, 2), W.integer(m, n, 3)
@@ -122,7 +122,7 @@ def test_classical_integer_bit_exact(m, n, k):
     assert np.array_equal(dC.cpu().numpy(), ref_gemm(A, B, C))
 
 
-@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_float_ragged_tolerance(levels, variant):
     case = float_case(255, 333, 517, 7, 8, 9, False)
@@ -131,7 +131,7 @@ def test_float_ragged_tolerance(levels, variant):
     check_float(dC.cpu().numpy(), levels, case)
 
 
-@pytest.mark.parametrize("levels", [0, 1, 2])
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_config_1024(levels, variant):
     """m = n = k = 1024, lda = ldb = ldc = 1024, uniform[-1, 1] from a seed, C = 0."""
@@ -145,7 +145,7 @@ def test_leading_dimensions_and_padding_untouched():
     m, n, k = 97, 131, 77
     A, B, C = W.integer(m, k, 11), W.integer(k, n, 12), W.integer(m, n, 13)
     ref = ref_gemm(A, B, C)
-    for levels in (0, 1, 2):
+    for levels in (0, 1, 2, 3):
         for variant in VARIANTS:
             dA, dB = dev(A, ld=k + 3), dev(B, ld=n + 5)
             cbuf = torch.full((m, n + 7), 777.0, dtype=torch.float64, device="cuda")
@@ -161,7 +161,7 @@ def test_odd_leading_dimension_float():
     m, n, k = 200, 150, 301
     A, B, C = W.uniform(m, k, 14), W.uniform(k, n, 15), W.uniform(m, n, 16)
     ref = ref_gemm(A, B, C)
-    for levels in (1, 2):
+    for levels in (1, 2, 3):
         dC = dev(C, ld=n + 1)
         run(dev(A, ld=k + 1), dev(B, ld=n + 3), dC, levels, "ABC")
         assert normwise_err(dC.cpu().numpy(), ref, A, B) <= TOL[levels]
@@ -205,7 +205,7 @@ def test_runs_on_a_side_stream():
     assert np.array_equal(dC.cpu().numpy(), A @ B)
 
 
-@pytest.mark.parametrize("levels,variant", [(2, "ABC"), (1, "ABC"), (0, "classical")])
+@pytest.mark.parametrize("levels,variant", [(3, "ABC"), (2, "ABC"), (1, "ABC"), (0, "classical")])
 def test_full_size_sampled_against_dot2(levels, variant):
     """The benchmark's size (m = n = k = 8192, accumulate mode), checked on sampled
     entries the oracle computes one by one with Dot2."""

@@ -58,9 +58,14 @@ def test_bit_exact_with_spread_exponents(sigma):
         assert np.array_equal(run(A, B, C, levels), ozaki.gemm(A, B, C, levels))
 
 
+def test_three_levels_bit_exact_against_the_scheme_oracle():
+    A, B, C = W.uniform(130, 150, 1), W.uniform(150, 70, 2), W.uniform(130, 70, 3)
+    assert np.array_equal(run(A, B, C, 3), ozaki.gemm(A, B, C, 3))
+
+
 def test_integer_inputs_exact():
     A, B, C = W.integer(100, 90, 7), W.integer(90, 80, 8), W.integer(100, 80, 9)
-    for levels in (0, 1, 2):
+    for levels in (0, 1, 2, 3):
         assert np.array_equal(run(A, B, C, levels), C + A @ B)
 
 

@@ -155,7 +155,33 @@ def test_two_levels_equal_one_level_twice():
     assert np.array_equal(two, brute(A, B, np.zeros((20, 18))))
 
 
-@pytest.mark.parametrize("levels,tol", [(1, 1e-13), (2, 1e-12)])
+def test_three_levels_recursive_flat_and_bruteforce_agree():
+    """Sections 3.5-3.6 one level further: recursive three-level Strassen, the flat
+    343-product table of Eq. 4 and brute force agree bit for bit on integers, on a
+    ragged shape whose blocks are padded at every level."""
+    A, B, C = W.integer(37, 29, 15), W.integer(29, 41, 16), W.integer(37, 41, 17)
+    rec = C.copy()
+    oracle.strassen(A, B, rec, 3)
+    flat = tables.apply_table(A, B, C, 3)
+    ref = brute(A, B, C)
+    assert np.array_equal(rec, ref)
+    assert np.array_equal(flat, ref)
+
+
+def test_three_level_table_is_the_associative_kronecker_cube():
+    """The three-level table built as (two-level) x (Figure 1) equals the one built as
+    (Figure 1) x (two-level) with product index 49 a + b and block index 4 outer + inner:
+    the Kronecker product is associative, so both orders name the same 343 products."""
+    def kron(outer, inner, w):
+        return tuple((w * oi + ii, w * oj + ij, os * s) for (oi, oj, os) in outer for (ii, ij, s) in inner)
+    other = [(kron(fa, ta, 4), kron(fb, tb, 4), kron(fc, tc, 4))
+             for (fa, fb, fc) in tables.FIG1 for (ta, tb, tc) in tables.table(2)]
+    assert other == tables.table(3)
+    c3 = tables.counts(3)
+    assert c3["products"] == 343 and c3["a_terms"] == 12 ** 3 and c3["c_updates"] == 12 ** 3
+
+
+@pytest.mark.parametrize("levels,tol", [(1, 1e-13), (2, 1e-12), (3, 1e-12)])
 def test_strassen_float_error_scale(levels, tol):
     n = 192
     A, B = W.uniform(n, n, 11), W.uniform(n, n, 12)

@@ -61,6 +61,7 @@ CASES = [
     (1000, 999, 1001, 1, False),
     (1024, 1024, 1024, 2, False),
     (8192, 8192, 96, 2, True),   # M uses the whole array: (8192/4)^2 = 4 Mi doubles
+    (301, 203, 150, 3, True),
 ]
 
 
@@ -102,4 +103,4 @@ def test_no_alloc_rejects_products_beyond_the_array():
     assert st == -10, sg.strassen_status_string(st)
     torch.cuda.synchronize()
     assert torch.all(C == 5.0)
-    assert sg.strassen_gemm_ab_noalloc(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n, 3, 0) == -4
+    assert sg.strassen_gemm_ab_noalloc(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n, 4, 0) == -4
