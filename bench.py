@@ -70,9 +70,19 @@ def dist_info():
 
 
 def algorithmic_flops(m, n, k, levels):
-    """FP64 flops the method performs: 7^L products of 2 h_m h_n h_k (Section 3.1-3.2)
-    plus the extra additions of the performance model's T_a (Section 4.2) with the
-    operand and C term counts of the L-level table."""
+    """FP64-pipe flops of the method: 7^L products of 2 h_m h_n h_k multiply-add flops
+    (Sections 3.1-3.2).  The extra additions of the performance model's T_a (Section
+    4.2) are not on the FP64 pipe here (operand sums on the integer pipe, C updates as
+    L2 atomics): see model_flops."""
+    P = 1 << levels
+    hm, hn, hk = -(-m // P), -(-n // P), -(-k // P)
+    return 7 ** levels * 2.0 * hm * hn * hk
+
+
+def model_flops(m, n, k, levels):
+    """The paper's arithmetic count T_a / tau_a (Section 4.2): the products plus two flops
+    per extra addition of A and B blocks and per C update, with the term counts of the
+    L-level table."""
     from paper_1605_01078_gb300 import strassen_plan_table
     P = 1 << levels
     hm, hn, hk = -(-m // P), -(-n // P), -(-k // P)
@@ -80,7 +90,7 @@ def algorithmic_flops(m, n, k, levels):
     a_adds = sum(len(p[0]) - 1 for p in tab)
     b_adds = sum(len(p[1]) - 1 for p in tab)
     c_upd = sum(len(p[2]) for p in tab) if levels > 0 else 0
-    return len(tab) * 2.0 * hm * hn * hk + 2.0 * (a_adds * hm * hk + b_adds * hk * hn + c_upd * hm * hn)
+    return algorithmic_flops(m, n, k, levels) + 2.0 * (a_adds * hm * hk + b_adds * hk * hn + c_upd * hm * hn)
 
 
 class ClockSampler:
@@ -247,13 +257,30 @@ def bench_split_precision(sg, W, torch, n=8192, err_n=4096, reps=3):
     return out
 
 
+def level_error(sg, torch, A, B, C, stream, levels, variant="ABC"):
+    """max|C_L - C_0| / (||A||_inf max|B|) of one call against the library's classical
+    result on the same inputs (the normwise reading of the tolerance)."""
+    ref = C.clone()
+    sg.classical(A, B, ref)
+    got = C.clone()
+    sg.gemm(A, B, got, levels=levels, variant=variant, stream=stream)
+    torch.cuda.synchronize()
+    den = float(A.abs().sum(dim=1).max()) * float(B.abs().max())
+    err = float((got - ref).abs().max()) / den
+    del ref, got
+    return err
+
+
 def bench_other_levels(sg, torch, A, B, C, stream, levels_list, variant="ABC", reps=3):
     """The same product with other level counts (on the same resident inputs): effective
-    GFLOP/s and the FP64 pipe fraction of each, CUDA events per call."""
+    GFLOP/s and the FP64 pipe fraction of each (CUDA events per call), and the max-norm
+    error of one call against the library's classical result on the same C
+    (max|C_L - C_0| / (||A||_inf max|B|))."""
     m, k = A.shape
     n = B.shape[1]
     out = {}
     for lv in levels_list:
+        err = level_error(sg, torch, A, B, C, stream, lv, variant)
         sg.gemm(A, B, C, levels=lv, variant=variant, stream=stream)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -265,7 +292,8 @@ def bench_other_levels(sg, torch, A, B, C, stream, levels_list, variant="ABC", r
         t = statistics.median(a.elapsed_time(b) / 1e3 for a, b in ev)
         alg = algorithmic_flops(m, n, k, lv) / t / 1e9
         out[str(lv)] = {"value": 2.0 * m * n * k / t / 1e9, "unit": UNIT, "ms": t * 1e3,
-                        "variant": variant, "algorithmic_gflops": alg, "frac": alg / FP64_PEAK_GFLOPS}
+                        "variant": variant, "algorithmic_gflops": alg, "frac": alg / FP64_PEAK_GFLOPS,
+                        "err_vs_classical": err}
     return out
 
 
@@ -423,6 +451,9 @@ def main():
                "h2d_bytes_per_step": int(3 * 8 * m * n), "d2h_bytes_per_step": int(8 * m * n)}
         del dA, dB, dC
 
+    err_headline = None
+    if args.dtype == "f64" and rank == 0 and m <= 8192:
+        err_headline = level_error(sg, torch, A, B, C, stream, L, variant)
     levels_other = None
     if not args.no_levels and args.dtype == "f64" and rank == 0:
         levels_other = bench_other_levels(sg, torch, A, B, C, stream, [lv for lv in (1, 2, 3) if lv != L])
@@ -479,6 +510,7 @@ def main():
                    "m": m, "n": n, "k": k, "levels": L, "variant": variant, "products": args.dtype,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (3 x 8 m n bytes)"},
         "classical": {"value": cls_val, "unit": UNIT, "speedup": value / ws / cls_val},
+        "err_vs_classical": err_headline,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

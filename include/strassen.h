@@ -174,7 +174,7 @@ STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
 
 /*
  * strassen_select -- the variant selector: picks which member of the family (classical,
- * or 1 / 2 levels of ABC, AB or Naive; tile_id is always 0, the 128x128x8 tile) to
+ * or 1 / 2 / 3 levels of ABC, AB or Naive; tile_id is always 0, the 128x128x8 tile) to
  * run for an m x n x k product in `dtype` -- the choice Section 4.2 of the paper
  * builds its performance model for.  In order of precedence it returns
  *   1. the exhaustive-measurement record for exactly this shape and dtype, if one was
@@ -182,8 +182,10 @@ STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
  *   2. the argmin of the learned selector's predictions, if a network was loaded with
  *      strassen_selector_load() (one small kernel launch on a library stream, then a
  *      wait for its result);
- *   3. the analytic model's argmin (strassen_model_seconds) otherwise (FP64), or
- *      classical slices (split-precision dtypes).
+ *   3. the analytic model's argmin (strassen_model_seconds, levels 0 to 3) otherwise
+ *      (FP64), or classical slices (split-precision dtypes).
+ * The learned selector's candidates stop at two levels (its output layer has the 7
+ * candidates listed below); exhaustive records may hold any level.
  * The model prefers fewer levels on ties within 1 %.
  *
  *   levels, variant, tile_id   outputs (host pointers, non-NULL).

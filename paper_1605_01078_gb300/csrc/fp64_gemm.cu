@@ -383,30 +383,47 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       uint64_t* sa = reinterpret_cast<uint64_t*>(sumA + q * BK * BM);
       uint64_t* sb = reinterpret_cast<uint64_t*>(sumB + q * BK * BN);
       const int64_t k0 = (int64_t)cur.ks * BK;
+      // Each producer thread owns row pt of the A tile (its BK values are contiguous in
+      // the raw box) and column pt of the B tile.  The sums run term by term over all of
+      // the thread's elements, so the BK chains of additions are independent and
+      // interleave; each chain still adds the terms left to right.
+      static_assert(BM == kProducers && BN == kProducers && BK == 8, "producer element mapping");
+      {
+        uint64_t v[BK];
+        const uint64_t s0 = (uint64_t)term_neg(c_plans.ta[row][0]) << 63;
+        const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(ra + pt * BK);
 #pragma unroll
-      for (int qq = 0; qq < (BM * BK) / kProducers; ++qq) {
-        const int e = pt + qq * kProducers;
-        const int kk = e / BM, i = e - (e / BM) * BM;
-        uint64_t v = 0;
-        if (k0 + kk < d.hk) {
-          const int src = i * BK + kk;
-          v = ra[src] ^ ((uint64_t)term_neg(c_plans.ta[row][0]) << 63);
-          for (int t = 1; t < na; ++t)
-            v = int_fadd_bits(v, ra[t * BM * BK + src] ^ ((uint64_t)term_neg(c_plans.ta[row][t]) << 63));
+        for (int h = 0; h < BK / 2; ++h) {
+          const ulonglong2 w = r0[h];
+          v[2 * h] = w.x ^ s0;
+          v[2 * h + 1] = w.y ^ s0;
         }
-        sa[e] = v;
+        for (int t = 1; t < na; ++t) {
+          const uint64_t st = (uint64_t)term_neg(c_plans.ta[row][t]) << 63;
+          const ulonglong2* rt = reinterpret_cast<const ulonglong2*>(ra + t * BM * BK + pt * BK);
+#pragma unroll
+          for (int h = 0; h < BK / 2; ++h) {
+            const ulonglong2 w = rt[h];
+            v[2 * h] = int_fadd_bits(v[2 * h], w.x ^ st);
+            v[2 * h + 1] = int_fadd_bits(v[2 * h + 1], w.y ^ st);
+          }
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) sa[kk * BM + pt] = (k0 + kk < d.hk) ? v[kk] : 0;
       }
+      {
+        uint64_t v[BK];
+        const uint64_t s0 = (uint64_t)term_neg(c_plans.tb[row][0]) << 63;
 #pragma unroll
-      for (int qq = 0; qq < (BN * BK) / kProducers; ++qq) {
-        const int e = pt + qq * kProducers;
-        const int kk = e / BN;
-        uint64_t v = 0;
-        if (k0 + kk < d.hk) {
-          v = rb[e] ^ ((uint64_t)term_neg(c_plans.tb[row][0]) << 63);
-          for (int t = 1; t < nb; ++t)
-            v = int_fadd_bits(v, rb[t * BK * BN + e] ^ ((uint64_t)term_neg(c_plans.tb[row][t]) << 63));
+        for (int kk = 0; kk < BK; ++kk) v[kk] = rb[kk * BN + pt] ^ s0;
+        for (int t = 1; t < nb; ++t) {
+          const uint64_t st = (uint64_t)term_neg(c_plans.tb[row][t]) << 63;
+          const uint64_t* rt = rb + t * BK * BN + pt;
+#pragma unroll
+          for (int kk = 0; kk < BK; ++kk) v[kk] = int_fadd_bits(v[kk], rt[kk * BN] ^ st);
         }
-        sb[e] = v;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) sb[kk * BN + pt] = (k0 + kk < d.hk) ? v[kk] : 0;
       }
       mbar_arrive(&sum_full[q]);
       mbar_arrive(&raw_empty[slot]);

@@ -33,77 +33,59 @@ inline double ifa_double(uint64_t b) {
 }
 #endif
 
-// Shift right by n (0 <= n), OR-ing every bit shifted out into bit 0 ("jamming").
-__host__ __device__ __forceinline__ uint64_t ifa_shr_jam(uint64_t x, int n) {
-  if (n == 0) return x;
-  if (n >= 64) return x != 0 ? 1 : 0;
-  return (x >> n) | ((x << (64 - n)) != 0 ? 1 : 0);
-}
-
-// Round s (value s * 2^(e - 1078): three extra low bits; the leading one at bit 55 for a
-// normal result, below it only when e == 1, i.e. a subnormal result) to nearest even
-// and pack it with `sign`.
-__host__ __device__ __forceinline__ uint64_t ifa_round_pack(uint64_t sign, int e, uint64_t s) {
-  const uint64_t low = s & 7;
-  uint64_t sig = s >> 3;
-  if (low > 4 || (low == 4 && (sig & 1))) sig += 1;
-  if (sig >> 53) {  // rounding carried into a new binade
-    sig >>= 1;
-    e += 1;
-  }
-  if (e >= 2047) return sign | 0x7ff0000000000000ULL;  // overflow to infinity
-  if (sig < (1ULL << 52)) return sign | sig;             // subnormal: exponent field 0
-  return sign | ((uint64_t)e << 52) | (sig & ((1ULL << 52) - 1));
-}
-
 // The bits of a + b (b's sign bit already flipped for a subtraction), rounded to
 // nearest even; operands and result are binary64 bit patterns, so no value of floating
-// type (and no floating-point instruction) appears in the computation.
+// type (and no floating-point instruction) appears in the computation.  Written without
+// data-dependent branches (the add and subtract cases, the alignment shift, the
+// normalisation and the special operands are all selects), so the lanes of a warp stay
+// converged and the compiler can interleave independent additions.
 __host__ __device__ __forceinline__ uint64_t int_fadd_bits(uint64_t ua, uint64_t ub) {
   const uint64_t kExpMask = 0x7ff0000000000000ULL, kMag = 0x7fffffffffffffffULL;
-  // Infinities and NaNs: rare; follow the definition of IEEE addition.
-  if ((ua & kExpMask) == kExpMask || (ub & kExpMask) == kExpMask) {
-    const bool nan_a = (ua & kMag) > kExpMask, nan_b = (ub & kMag) > kExpMask;
-    if (nan_a || nan_b) return 0x7ff8000000000000ULL;
-    const bool inf_a = (ua & kMag) == kExpMask, inf_b = (ub & kMag) == kExpMask;
-    if (inf_a && inf_b) return ((ua ^ ub) >> 63) ? 0x7ff8000000000000ULL : ua;
-    return inf_a ? ua : ub;
-  }
-  // Zeros: x + 0 = x; (+0) + (-0) = +0 and (-0) + (-0) = -0 under round to nearest.
-  if ((ub & kMag) == 0) return (ua & kMag) == 0 ? (ua & ub) : ua;
-  if ((ua & kMag) == 0) return ub;
-  // Order by magnitude: |a| >= |b|.
-  if ((ub & kMag) > (ua & kMag)) {
-    const uint64_t t = ua;
-    ua = ub;
-    ub = t;
-  }
-  const uint64_t sign = ua & 0x8000000000000000ULL;
-  int ea = (int)((ua >> 52) & 0x7ff), eb = (int)((ub >> 52) & 0x7ff);
-  uint64_t ma = ua & ((1ULL << 52) - 1), mb = ub & ((1ULL << 52) - 1);
-  if (ea) ma |= 1ULL << 52; else ea = 1;  // subnormals: no hidden bit, exponent 1
-  if (eb) mb |= 1ULL << 52; else eb = 1;
-  ma <<= 3;  // guard, round and sticky bits
-  mb = ifa_shr_jam(mb << 3, ea - eb);
-  uint64_t s;
-  int e = ea;
-  if (((ua ^ ub) >> 63) == 0) {
-    s = ma + mb;
-    if (s >> 56) {  // carry out of the 53 + 3 bit field
-      s = ifa_shr_jam(s, 1);
-      e += 1;
-    }
-  } else {
-    s = ma - mb;                       // >= 0 since |a| >= |b|
-    if (s == 0) return 0;  // exact cancellation gives +0
-    const int lz = ifa_clz64(s) - 8;   // the leading one belongs at bit 55
-    if (lz > 0) {
-      const int shift = lz < e - 1 ? lz : e - 1;  // never below the subnormal exponent
-      s <<= shift;
-      e -= shift;
-    }
-  }
-  return ifa_round_pack(sign, e, s);
+  const uint64_t kFrac = (1ULL << 52) - 1, kHidden = 1ULL << 52, kQNaN = 0x7ff8000000000000ULL;
+  const uint64_t am = ua & kMag, bm = ub & kMag;
+  const bool sub = ((ua ^ ub) >> 63) != 0;
+  // x: the operand of larger magnitude (it gives the sign), y: the other.
+  const bool swap = bm > am;
+  const uint64_t x = swap ? ub : ua;
+  const uint64_t xm = swap ? bm : am, ym = swap ? am : bm;
+  const int ex_f = (int)(xm >> 52), ey_f = (int)(ym >> 52);
+  // Significands with the hidden bit (none for subnormals and zeros, whose exponent
+  // reads as 1), scaled by 8 for the guard, round and sticky bits.
+  const uint64_t mx = ((xm & kFrac) | (ex_f ? kHidden : 0)) << 3;
+  uint64_t my = ((ym & kFrac) | (ey_f ? kHidden : 0)) << 3;
+  const int ex = ex_f + (ex_f == 0), ey = ey_f + (ey_f == 0);
+  // Align y to x's exponent, OR-ing every bit shifted out into bit 0 (my < 2^56, so
+  // any shift of 63 or more leaves only the sticky bit).
+  const int d = (ex - ey) < 63 ? (ex - ey) : 63;
+  my = (my >> d) | ((my & ((1ULL << d) - 1)) != 0 ? 1 : 0);
+  uint64_t s = sub ? mx - my : mx + my;  // >= 0 since |x| >= |y|
+  const bool zero = s == 0;
+  // Normalise so the leading one sits at bit 55: one right shift (with sticky) after a
+  // carry out of an addition, else a left shift after cancellation, never below the
+  // subnormal exponent 1.
+  const bool carry = (s >> 56) != 0;
+  const int lz = ifa_clz64(s) - 8;
+  const int sh = carry ? 0 : (lz < ex - 1 ? lz : ex - 1);
+  s = carry ? ((s >> 1) | (s & 1)) : (s << sh);
+  const int e = carry ? ex + 1 : ex - sh;
+  // Round to nearest even on the three extra bits.
+  const uint64_t low = s & 7;
+  uint64_t sig = s >> 3;
+  sig += (low > 4 || (low == 4 && (sig & 1))) ? 1 : 0;
+  // Pack: (e - 1) << 52 plus the significand with its hidden bit gives the exponent
+  // field e for a normal result, 0 for a subnormal (no hidden bit, e == 1), and carries
+  // a rounding overflow (sig == 2^53) into the next binade.  Anything at or above the
+  // infinity pattern overflowed.
+  uint64_t r = ((uint64_t)(e - 1) << 52) + sig;
+  r = (x & 0x8000000000000000ULL) | (r >= kExpMask ? kExpMask : r);
+  // A zero sum: +0 from exact cancellation, or (+-0) + (+-0) = +0 unless both are -0.
+  r = zero ? (xm == 0 ? (ua & ub) : 0) : r;
+  // Infinities and NaNs (IEEE addition): NaN in -> quiet NaN; inf + (-inf) -> NaN;
+  // otherwise the infinity.
+  const bool nan_in = am > kExpMask || bm > kExpMask;
+  const bool inf_a = am == kExpMask, inf_b = bm == kExpMask;
+  const uint64_t special = (nan_in || (inf_a && inf_b && sub)) ? kQNaN : (inf_a ? ua : ub);
+  return (am >= kExpMask || bm >= kExpMask) ? special : r;
 }
 
 // a + b, or a - b when `negate_b`, rounded to nearest even.

@@ -1,5 +1,5 @@
-// Variant selection: which member of the family (classical, 1 or 2 levels of ABC, AB
-// or Naive) to run for a shape.  Section 4.2 of the paper proposes its performance
+// Variant selection: which member of the family (classical, 1, 2 or 3 levels of ABC,
+// AB or Naive) to run for a shape.  Section 4.2 of the paper proposes its performance
 // model for exactly this choice, by problem size and thread count.
 //
 // Order of precedence in strassen_select():
@@ -101,7 +101,7 @@ double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant) {
 void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant) {
   double best = model_seconds(m, n, k, 0, STRASSEN_ABC);
   int bl = 0, bv = STRASSEN_ABC;
-  for (int L = 1; L <= 2; ++L) {
+  for (int L = 1; L <= kMaxLevels; ++L) {
     if (((int64_t)1 << L) > m || ((int64_t)1 << L) > n || ((int64_t)1 << L) > k) break;
     for (int v : {STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE}) {
       const double t = model_seconds(m, n, k, L, v);

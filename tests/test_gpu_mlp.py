@@ -105,4 +105,4 @@ def test_select_uses_the_loaded_network():
         sg.strassen_tune_clear()
         sg.strassen_selector_clear()
     lv, var, _ = sg.strassen_select(8192, 8192, 8192, sg.STRASSEN_F64)
-    assert lv == 2  # back to the analytic model
+    assert lv == 3  # back to the analytic model (three levels at 8192^3)
