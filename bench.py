@@ -376,7 +376,7 @@ def main():
 
     launches_per_step = 1 if (L == 0 or variant.upper() == "ABC") else None
     if args.dtype == "oz_bf16":
-        launches_per_step = 4  # split rows, split columns, slice products, recombine + scatter
+        launches_per_step = 5  # split rows, column maxima, split columns, slice products, recombine + scatter
     elif launches_per_step is None:
         nprod = 7 ** L
         launches_per_step = nprod * (2 if variant.upper() == "AB" else 4)

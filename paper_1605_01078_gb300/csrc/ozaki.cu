@@ -4,7 +4,7 @@
 // computed from integer slices of its two FP64 operands (the error-free splitting of
 // Ozaki, Ogita, Oishi and Rump, carried out on integer digits):
 //
-//   1. split (oz_split_rows / oz_split_cols): form the operand sum in FP64; scale each
+//   1. split (oz_split_rows; oz_colmax + oz_split_cols): form the operand sum; scale each
 //      row of X^ (column of V^) by 2^-e so that it lies in (-1/2, 1/2), with e the
 //      smallest integer such that the row maximum is below 2^(e-1); round to the
 //      integer N = rint(x 2^(56 - e)) -- an exact scaling followed by round-to-nearest-
@@ -184,39 +184,66 @@ __global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
   }
 }
 
-// One block per 64 output columns j of V^ (columns of B's operand sum), product
-// blockIdx.y.  The slices are written transposed ([j][k], k contiguous) through a
-// shared-memory tile.
-constexpr int kColTilePitch = 64 + 8;  // bf16 per tile row (padding against bank conflicts)
-constexpr size_t kSplitColsSmem = sizeof(__nv_bfloat16) * kS * 64 * kColTilePitch;
+// Column maxima of V^ (B's operand sum) for the per-column scales: one block per 64
+// columns x kColMaxRows rows of the reduction dimension, product blockIdx.z; partial
+// maxima of the magnitude bits meet in `colmax_bits` (cleared before) by atomicMax
+// (magnitude order equals the order of the bit patterns of non-negative doubles).
+constexpr int kColMaxRows = 256;
 
-__global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ SplitArgs a) {
-  __shared__ unsigned long long colmax[4][64];
-  extern __shared__ __align__(16) __nv_bfloat16 tile_raw[];  // [kS][64][kColTilePitch]
-  auto tile = [&](int s, int c, int k) -> __nv_bfloat16& { return tile_raw[(s * 64 + c) * kColTilePitch + k]; };
-  const int p = blockIdx.y;
+__global__ void __launch_bounds__(256) oz_colmax(const __grid_constant__ SplitArgs a,
+                                                 unsigned long long* colmax_bits) {
+  __shared__ unsigned long long red[4][64];
+  const int p = blockIdx.z;
   const int64_t j0 = (int64_t)blockIdx.x * 64;
+  const int64_t kb = (int64_t)blockIdx.y * kColMaxRows;
+  const int64_t ke = kb + kColMaxRows < a.h_k ? kb + kColMaxRows : a.h_k;
   const int row = a.plan_off + p;
   const int nt = c_oz_plans.nb[row];
   uint8_t terms[kMaxTerms];
   for (int t = 0; t < kMaxTerms; ++t) terms[t] = c_oz_plans.tb[row][t];
   const int tid = threadIdx.x, c = tid & 63, ph = tid >> 6;
-  // Column maxima over the reduction dimension (rows of B's operand sum).
   unsigned long long mx = 0;
   if (j0 + c < a.h_out)
-    for (int64_t k = ph; k < a.h_k; k += 4)
+    for (int64_t k = kb + ph; k < ke; k += 4)
       mx = max(mx, mag_bits(operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j0 + c)));
-  colmax[ph][c] = mx;
+  red[ph][c] = mx;
   __syncthreads();
   if (tid < 64) {
-    const unsigned long long v = max(max(colmax[0][tid], colmax[1][tid]), max(colmax[2][tid], colmax[3][tid]));
-    colmax[0][tid] = v;
-    if (j0 + tid < a.h_outp) a.exps[(int64_t)p * a.h_outp + j0 + tid] = (j0 + tid < a.h_out) ? scale_exponent(v) : 0;
+    const unsigned long long v = max(max(red[0][tid], red[1][tid]), max(red[2][tid], red[3][tid]));
+    if (v != 0 && j0 + tid < a.h_out) atomicMax(&colmax_bits[(int64_t)p * a.h_outp + j0 + tid], v);
+  }
+}
+
+// One block per 64 output columns j x 64 reduction indices k of V^, product blockIdx.z:
+// the digits of the scaled column entries, written transposed ([j][k], k contiguous)
+// through a shared-memory tile.  The block row blockIdx.y == 0 also stores the scale
+// exponents.
+constexpr int kColTilePitch = 64 + 8;  // bf16 per tile row (padding against bank conflicts)
+constexpr size_t kSplitColsSmem = sizeof(__nv_bfloat16) * kS * 64 * kColTilePitch;
+
+__global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ SplitArgs a,
+                                                     const unsigned long long* colmax_bits) {
+  __shared__ int ecol[64];
+  extern __shared__ __align__(16) __nv_bfloat16 tile_raw[];  // [kS][64][kColTilePitch]
+  auto tile = [&](int s, int c, int k) -> __nv_bfloat16& { return tile_raw[(s * 64 + c) * kColTilePitch + k]; };
+  const int p = blockIdx.z;
+  const int64_t j0 = (int64_t)blockIdx.x * 64;
+  const int64_t k0 = (int64_t)blockIdx.y * 64;
+  const int row = a.plan_off + p;
+  const int nt = c_oz_plans.nb[row];
+  uint8_t terms[kMaxTerms];
+  for (int t = 0; t < kMaxTerms; ++t) terms[t] = c_oz_plans.tb[row][t];
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    const int64_t j = j0 + tid;
+    const int e = j < a.h_out ? scale_exponent(colmax_bits[(int64_t)p * a.h_outp + j]) : 0;
+    ecol[tid] = e;
+    if (blockIdx.y == 0 && j < a.h_outp) a.exps[(int64_t)p * a.h_outp + j] = e;
   }
   __syncthreads();
   const int64_t slice_stride = a.h_outp * a.h_kp;
   __nv_bfloat16* out = a.slices + (int64_t)p * kS * slice_stride;
-  for (int64_t k0 = 0; k0 < a.h_kp; k0 += 64) {
+  {
     for (int q = 0; q < 16; ++q) {
       const int e = tid + 256 * q;
       const int kk = e >> 6, cc = e & 63;
@@ -225,7 +252,7 @@ __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ Spl
       long long N = 0;
       if (j < a.h_out && k < a.h_k) {
         const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j);
-        N = scaled_rint(x, scale_exponent(colmax[0][cc]));
+        N = scaled_rint(x, ecol[cc]);
       }
       digits_of(N, d);
 #pragma unroll
@@ -243,7 +270,6 @@ __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ Spl
         dstv[1] = srcv[1];
       }
     }
-    __syncthreads();
   }
 }
 
@@ -641,7 +667,7 @@ int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
   const int64_t P = kPlanCount[levels];
   const int64_t hmp = round_up(block_edge(m, levels), kTM), hnp = round_up(block_edge(n, levels), kTN),
                 hkp = round_up(block_edge(k, levels), kTK);
-  return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + 2 * P * hmp * hnp * 8 + 4096;
+  return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + 2 * P * hmp * hnp * 8 + P * hnp * 8 + 4096;
 }
 
 int ozaki_device_status() {
@@ -670,7 +696,8 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   int* fx = (int*)w;                                           w += (size_t)P * hnp * 4;
   w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
   long long* thi = (long long*)w;                              w += (size_t)P * hmp * hnp * 8;
-  long long* tlo = (long long*)w;
+  long long* tlo = (long long*)w;                              w += (size_t)P * hmp * hnp * 8;
+  unsigned long long* colmax = (unsigned long long*)w;  // [P][h_np] magnitude bits
 
   SplitArgs sa;
   sa.src = A; sa.ld = lda; sa.rows = m; sa.cols = k; sa.h_r = hm; sa.h_c = hk;
@@ -690,7 +717,14 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   sb.src = B; sb.ld = ldb; sb.rows = k; sb.cols = n; sb.h_r = hk; sb.h_c = hn;
   sb.h_out = hn; sb.h_outp = hnp; sb.h_k = hk; sb.h_kp = hkp;
   sb.plan_off = kPlanOffset[levels]; sb.slices = DV; sb.exps = fx;
-  oz_split_cols<<<dim3((unsigned)(hnp / 64), (unsigned)P), 256, kSplitColsSmem, stream>>>(sb);
+  e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)P * hnp, stream);
+  if (e != cudaSuccess) return e;
+  oz_colmax<<<dim3((unsigned)(hnp / 64), (unsigned)((hk + kColMaxRows - 1) / kColMaxRows), (unsigned)P), 256, 0,
+              stream>>>(sb, colmax);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_split_cols<<<dim3((unsigned)(hnp / 64), (unsigned)(hkp / 64), (unsigned)P), 256, kSplitColsSmem, stream>>>(
+      sb, colmax);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
