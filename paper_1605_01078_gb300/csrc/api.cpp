@@ -49,9 +49,10 @@ int clamp_levels(int levels, int64_t m, int64_t n, int64_t k) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA; }
 
 int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                  int64_t ldb, double* C, int64_t ldc, EpilogueKind owner_epi, cudaStream_t s) {
+                  int64_t ldb, double* C, int64_t ldc, EpilogueKind owner_epi, cudaStream_t s, int tile = -1) {
   Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, C, ldc, 0);
   L.epi = owner_epi;
+  L.tile = tile;
   choose_fp64_schedule(&L, deterministic_requested());
   if (owner_epi == kEpiStore) {
     // The kernel accumulates into its target: a store is a clear followed by the adds.
@@ -62,9 +63,10 @@ int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
 }
 
 int run_abc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-            int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
+            int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile) {
   Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, C, ldc, levels);
   L.epi = kEpiAtomicAdd;
+  L.tile = tile;
   choose_fp64_schedule(&L, deterministic_requested());
   return cuda_status(launch_fp64(L, s));
 }
@@ -78,7 +80,7 @@ struct Workspace {
 };
 
 int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-           int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
+           int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile) {
   Plan pl;
   if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels);
@@ -97,6 +99,7 @@ int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
     L.prod_begin = r; L.nprod = 1;
     L.m_target = 1;
     L.epi = kEpiStore;
+    L.tile = tile;
     choose_fp64_schedule(&L, deterministic_requested());
     // The kernel accumulates into M: clear it first.
     if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
@@ -110,7 +113,7 @@ int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
 }
 
 int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-              int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s) {
+              int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile) {
   Plan pl;
   if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
@@ -130,7 +133,7 @@ int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, con
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
     e = launch_block_sum(V, hk, hn, B, ldb, k, n, hk, hn, pl.tb[r], pl.nb[r], s);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
-    int st = run_classical(hm, hn, hk, X, hk, V, hn, M, hn, kEpiStore, s);
+    int st = run_classical(hm, hn, hk, X, hk, V, hn, M, hn, kEpiStore, s, tile);
     if (st != STRASSEN_OK) return st;
     e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
@@ -165,26 +168,30 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
     if (chk < 0) return chk;
     if (chk == 1) return STRASSEN_OK;
     if (dtype == STRASSEN_F64_OZ_INT8) return STRASSEN_ERR_UNSUPPORTED;
+    int tile = -1;  // the launch's own choice unless the selector picked the whole plan
     if (levels == -1 || variant == STRASSEN_AUTO) {
-      int sl = 0, tile = 0;
+      int sl = 0, st_tile = 0;
       strassen_variant sv = STRASSEN_ABC;
-      const int st = strassen_select(m, n, k, dtype, &sl, &sv, &tile);
+      const int st = strassen_select(m, n, k, dtype, &sl, &sv, &st_tile);
       if (st != STRASSEN_OK) return st;
+      if (levels == -1 && variant == STRASSEN_AUTO) tile = st_tile;
       if (levels == -1) levels = sl;
       if (variant == STRASSEN_AUTO) variant = sv;
     }
+    const int requested_levels = levels;
     levels = clamp_levels(levels, m, n, k);
+    if (levels != requested_levels) tile = -1;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaPeekAtLastError() != cudaSuccess) {
       cudaGetLastError();
       return STRASSEN_ERR_CUDA;
     }
     if (dtype == STRASSEN_F64_OZ_BF16) return run_oz(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
-    if (levels == 0) return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, s);
+    if (levels == 0) return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, s, tile);
     switch (variant) {
-      case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
-      case STRASSEN_AB: return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
-      case STRASSEN_NAIVE: return run_naive(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
+      case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile);
+      case STRASSEN_AB: return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile);
+      case STRASSEN_NAIVE: return run_naive(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile);
       default: return STRASSEN_ERR_UNSUPPORTED;
     }
   } catch (...) {
@@ -297,15 +304,23 @@ int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* 
                                 STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE};
     lv = kLv[cand];
     var = kVar[cand];
+    // the network picks levels and variant; the tile follows the analytic model
     tile = 0;
+    if (dtype == STRASSEN_F64) {
+      double best = 1e300;
+      for (int t = 0; t < kNumTiles; ++t) {
+        const double x = model_seconds(m, n, k, lv, var, t);
+        if (x < best) { best = x; tile = t; }
+      }
+    }
   } else {
     if (dtype == STRASSEN_F64) {
-      model_select(m, n, k, &lv, &var);
+      model_select(m, n, k, &lv, &var, &tile);
     } else {  // split precision: tensor-core products, no FP64 model; classical slices
       lv = 0;
       var = STRASSEN_ABC;
+      tile = 0;
     }
-    tile = 0;
   }
   *levels = lv;
   *variant = (strassen_variant)var;
@@ -318,7 +333,7 @@ int strassen_tune_record(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, 
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if (levels < 0 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
   if ((int)dtype < 0 || (int)dtype > 2 || (int)variant < 0 || (int)variant > 2) return STRASSEN_ERR_UNSUPPORTED;
-  if (tile_id != 0) return STRASSEN_ERR_ARG;
+  if (tile_id < 0 || tile_id >= kNumTiles) return STRASSEN_ERR_ARG;
   record_store(m, n, k, (int)dtype, levels, (int)variant, tile_id);
   return STRASSEN_OK;
 }
@@ -330,7 +345,9 @@ int strassen_tune_clear(void) {
 
 double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant) {
   if (m <= 0 || n <= 0 || k <= 0 || levels < 0 || levels > kMaxLevels || (int)variant < 0 || (int)variant > 2) return -1.0;
-  return model_seconds(m, n, k, levels, (int)variant);
+  double best = 1e300;
+  for (int t = 0; t < kNumTiles; ++t) best = std::min(best, model_seconds(m, n, k, levels, (int)variant, t));
+  return best;
 }
 
 int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, strassen_variant variant,
@@ -341,9 +358,9 @@ int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, str
     return STRASSEN_ERR_UNSUPPORTED;
   if (m == 0 || n == 0 || k == 0) return 0;
   if (levels == -1 || variant == STRASSEN_AUTO) {
-    int sl = 0, tile = 0;
+    int sl = 0, sel_tile = 0;
     strassen_variant sv = STRASSEN_ABC;
-    strassen_select(m, n, k, dtype, &sl, &sv, &tile);
+    strassen_select(m, n, k, dtype, &sl, &sv, &sel_tile);
     if (levels == -1) levels = sl;
     if (variant == STRASSEN_AUTO) variant = sv;
   }

@@ -52,18 +52,28 @@ namespace {
 __constant__ PlanTables c_plans = kPlanTables;
 __device__ int g_fp64_status;  // STRASSEN_ERR_TIMEOUT once a bounded wait gave up
 
-constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;
-constexpr int kConsumers = 256;  // 8 warps: 16 x 16 threads, 8 x 8 outputs each
+// Block tile BT x BT x BK: BT = 128 (tile id 0) or 64 (tile id 1, for small blocks where
+// 128-wide tiles would mostly compute padding).  The consumers are 16 x 16 threads with
+// a (BT/16) x (BT/16) register tile each.
+constexpr int BK = 8;
+constexpr int kTileIds = kNumTiles;
+constexpr int tile_edge(int tile_id) { return tile_id == 0 ? 128 : 64; }
+// Cost model of the tile choice (FMA-equivalents): a 64-wide k-step costs
+// kSmallTileFactor times its FMAs, and every k-step a fixed overhead for the hand-over
+// between the warp groups.
+constexpr double kStepOverheadFma = 2000.0;
+constexpr int kConsumers = 256;  // 8 warps: 16 x 16 threads
 constexpr int kProducers = 128;  // 4 warps: staging and operand sums
 constexpr int kThreads = kConsumers + kProducers;
 constexpr int NS = 4;  // ring of summed tiles
 // Ring of raw source tiles: two slots (the load of the next k-step overlaps the sums of
 // this one) while MAXT source tiles per operand fit twice in shared memory; one slot
-// for the eight-term products of three levels.  One k-step of the consumers takes
-// about 64K clocks of FP64 work per SM, so a producer that loads (about 1 us) and then
-// sums (a few us) each step still runs ahead of them through the summed ring.
-template <int MAXT>
-constexpr int raw_slots() { return MAXT >= 8 ? 1 : 2; }
+// for the eight-term products of three levels with 128-wide tiles.  One k-step of the
+// consumers takes about 64K clocks of FP64 work per SM (128-wide tiles), so a producer
+// that loads (about 1 us) and then sums (a few us) each step still runs ahead of them
+// through the summed ring.
+template <int MAXT, int BT>
+constexpr int raw_slots() { return (MAXT >= 8 && BT >= 128) ? 1 : 2; }
 constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 // Register split (setmaxnreg): the block is launched with kLaunchRegs per thread;
 // the producer warpgroup gives registers back and the two consumer warpgroups take
@@ -98,9 +108,10 @@ struct KArgs {
   int64_t total;           // stream-K: iterations of all problems; owner: tile positions
 };
 
-template <int MAXT>
+template <int MAXT, int BT>
 struct Smem {
-  static constexpr int NR = raw_slots<MAXT>();
+  static constexpr int BM = BT, BN = BT;
+  static constexpr int NR = raw_slots<MAXT, BT>();
   static constexpr int kRawA = MAXT * BM * BK;  // doubles per ring slot
   static constexpr int kRawB = MAXT * BK * BN;
   static constexpr size_t kBytes =
@@ -240,10 +251,11 @@ __device__ __forceinline__ void cursor_next(const KArgs& a, Cursor& c) {
 
 // ---------------------------------------------------------------- kernel
 
-template <int MAXT, bool BATCHED>
+template <int MAXT, bool BATCHED, int BT>
 __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid_constant__ KArgs a) {
-  using S = Smem<MAXT>;
+  using S = Smem<MAXT, BT>;
   constexpr int NR = S::NR;
+  constexpr int BM = BT, BN = BT, TM = BT / 16, TN = BT / 16;
   extern __shared__ __align__(128) double smem[];
   double* rawA = smem;                    // [NR][MAXT][BM][BK]   (TMA box layout: row, k)
   double* rawB = rawA + NR * S::kRawA;    // [NR][MAXT][BK][BN]
@@ -383,47 +395,49 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       uint64_t* sa = reinterpret_cast<uint64_t*>(sumA + q * BK * BM);
       uint64_t* sb = reinterpret_cast<uint64_t*>(sumB + q * BK * BN);
       const int64_t k0 = (int64_t)cur.ks * BK;
-      // Each producer thread owns row pt of the A tile (its BK values are contiguous in
-      // the raw box) and column pt of the B tile.  The sums run term by term over all of
-      // the thread's elements, so the BK chains of additions are independent and
-      // interleave; each chain still adds the terms left to right.
-      static_assert(BM == kProducers && BN == kProducers && BK == 8, "producer element mapping");
+      // Each producer thread owns EPT consecutive k of row pt % BM of the A tile
+      // (contiguous in the raw box) and of column pt % BN of the B tile.  The sums run
+      // term by term over all of the thread's elements, so its EPT chains of additions
+      // are independent and interleave; each chain still adds the terms left to right.
+      constexpr int EPT = BM * BK / kProducers;
+      static_assert(BM == BN && EPT * kProducers == BM * BK && EPT % 2 == 0, "producer element mapping");
+      const int pr = pt % BM, koff = (pt / BM) * EPT;
       {
-        uint64_t v[BK];
+        uint64_t v[EPT];
         const uint64_t s0 = (uint64_t)term_neg(c_plans.ta[row][0]) << 63;
-        const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(ra + pt * BK);
+        const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(ra + pr * BK + koff);
 #pragma unroll
-        for (int h = 0; h < BK / 2; ++h) {
+        for (int h = 0; h < EPT / 2; ++h) {
           const ulonglong2 w = r0[h];
           v[2 * h] = w.x ^ s0;
           v[2 * h + 1] = w.y ^ s0;
         }
         for (int t = 1; t < na; ++t) {
           const uint64_t st = (uint64_t)term_neg(c_plans.ta[row][t]) << 63;
-          const ulonglong2* rt = reinterpret_cast<const ulonglong2*>(ra + t * BM * BK + pt * BK);
+          const ulonglong2* rt = reinterpret_cast<const ulonglong2*>(ra + t * BM * BK + pr * BK + koff);
 #pragma unroll
-          for (int h = 0; h < BK / 2; ++h) {
+          for (int h = 0; h < EPT / 2; ++h) {
             const ulonglong2 w = rt[h];
             v[2 * h] = int_fadd_bits(v[2 * h], w.x ^ st);
             v[2 * h + 1] = int_fadd_bits(v[2 * h + 1], w.y ^ st);
           }
         }
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) sa[kk * BM + pt] = (k0 + kk < d.hk) ? v[kk] : 0;
+        for (int i = 0; i < EPT; ++i) sa[(koff + i) * BM + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
       }
       {
-        uint64_t v[BK];
+        uint64_t v[EPT];
         const uint64_t s0 = (uint64_t)term_neg(c_plans.tb[row][0]) << 63;
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) v[kk] = rb[kk * BN + pt] ^ s0;
+        for (int i = 0; i < EPT; ++i) v[i] = rb[(koff + i) * BN + pr] ^ s0;
         for (int t = 1; t < nb; ++t) {
           const uint64_t st = (uint64_t)term_neg(c_plans.tb[row][t]) << 63;
-          const uint64_t* rt = rb + t * BK * BN + pt;
+          const uint64_t* rt = rb + t * BK * BN + pr;
 #pragma unroll
-          for (int kk = 0; kk < BK; ++kk) v[kk] = int_fadd_bits(v[kk], rt[kk * BN] ^ st);
+          for (int i = 0; i < EPT; ++i) v[i] = int_fadd_bits(v[i], rt[(koff + i) * BN] ^ st);
         }
 #pragma unroll
-        for (int kk = 0; kk < BK; ++kk) sb[kk * BN + pt] = (k0 + kk < d.hk) ? v[kk] : 0;
+        for (int i = 0; i < EPT; ++i) sb[(koff + i) * BN + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
       }
       mbar_arrive(&sum_full[q]);
       mbar_arrive(&raw_empty[slot]);
@@ -552,33 +566,38 @@ constexpr int kMaxDev = 64;
 DeviceState g_dev[kMaxDev];
 std::mutex g_mu;
 
-template <int MAXT, bool BATCHED>
+template <int MAXT, bool BATCHED, int BT>
 const void* kernel_fn() {
-  return (const void*)fp64_strassen_kernel<MAXT, BATCHED>;
+  return (const void*)fp64_strassen_kernel<MAXT, BATCHED, BT>;
 }
 
-// Kernel instance by the largest term count of the launch's products: class c holds up
-// to 2^c source tiles per operand (c = 0..3).
+// Kernel instance by the largest term count of the launch's products -- class c holds
+// up to 2^c source tiles per operand (c = 0..3) -- and by the tile id.
 constexpr int kTermClasses = kMaxLevels + 1;
-template <bool BATCHED>
-const void* pick_kernel_b(int maxt_class) {
+template <bool BATCHED, int BT>
+const void* pick_kernel_bt(int maxt_class) {
   switch (maxt_class) {
-    case 0: return kernel_fn<1, BATCHED>();
-    case 1: return kernel_fn<2, BATCHED>();
-    case 2: return kernel_fn<4, BATCHED>();
-    default: return kernel_fn<8, BATCHED>();
+    case 0: return kernel_fn<1, BATCHED, BT>();
+    case 1: return kernel_fn<2, BATCHED, BT>();
+    case 2: return kernel_fn<4, BATCHED, BT>();
+    default: return kernel_fn<8, BATCHED, BT>();
   }
 }
-const void* pick_kernel(int maxt_class, bool batched) {
-  return batched ? pick_kernel_b<true>(maxt_class) : pick_kernel_b<false>(maxt_class);
+const void* pick_kernel(int maxt_class, bool batched, int tile_id) {
+  if (tile_id == 0) return batched ? pick_kernel_bt<true, 128>(maxt_class) : pick_kernel_bt<false, 128>(maxt_class);
+  return batched ? pick_kernel_bt<true, 64>(maxt_class) : pick_kernel_bt<false, 64>(maxt_class);
 }
-size_t smem_bytes(int maxt_class) {
+template <int BT>
+size_t smem_bytes_bt(int maxt_class) {
   switch (maxt_class) {
-    case 0: return Smem<1>::kBytes;
-    case 1: return Smem<2>::kBytes;
-    case 2: return Smem<4>::kBytes;
-    default: return Smem<8>::kBytes;
+    case 0: return Smem<1, BT>::kBytes;
+    case 1: return Smem<2, BT>::kBytes;
+    case 2: return Smem<4, BT>::kBytes;
+    default: return Smem<8, BT>::kBytes;
   }
+}
+size_t smem_bytes(int maxt_class, int tile_id) {
+  return tile_id == 0 ? smem_bytes_bt<128>(maxt_class) : smem_bytes_bt<64>(maxt_class);
 }
 
 cudaError_t ensure_device(int* sms_out) {
@@ -593,8 +612,9 @@ cudaError_t ensure_device(int* sms_out) {
     st.err = cudaDeviceGetAttribute(&st.sms, cudaDevAttrMultiProcessorCount, dev);
     for (int c = 0; c < kTermClasses && st.err == cudaSuccess; ++c)
       for (int b = 0; b < 2 && st.err == cudaSuccess; ++b)
-        st.err = cudaFuncSetAttribute(pick_kernel(c, b != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_bytes(c));
+        for (int t = 0; t < kTileIds && st.err == cudaSuccess; ++t)
+          st.err = cudaFuncSetAttribute(pick_kernel(c, b != 0, t), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_bytes(c, t));
     if (!g_encode && st.err == cudaSuccess) {
       cudaDriverEntryPointQueryResult q;
       void* fn = nullptr;
@@ -632,10 +652,11 @@ bool encode_2d(CUtensorMap* map, const double* base, int64_t rows, int64_t cols,
   return r == CUDA_SUCCESS;
 }
 
-// Fills a device descriptor from a launch.  TMA is used when every box coordinate the
-// kernel will issue is 16-byte aligned in the innermost dimension and the operands'
-// base addresses and row strides are 16-byte multiples.
+// Fills a device descriptor from a launch with the tile edge of L.tile.  TMA is used
+// when every box coordinate the kernel will issue is 16-byte aligned in the innermost
+// dimension and the operands' base addresses and row strides are 16-byte multiples.
 void fill_desc(const Fp64Launch& L, ProbDesc* d) {
+  const int BT = tile_edge(L.tile);
   std::memset(d, 0, sizeof(*d));
   d->A = L.A; d->B = L.B; d->C = L.C;
   d->lda = L.lda; d->ldb = L.ldb; d->ldc = L.ldc;
@@ -647,15 +668,15 @@ void fill_desc(const Fp64Launch& L, ProbDesc* d) {
   d->nprod = nprod;
   d->m_target = L.m_target;
   d->epi = L.epi;
-  d->tiles_m = (int)((L.hm + BM - 1) / BM);
-  d->tiles_n = (int)((L.hn + BN - 1) / BN);
+  d->tiles_m = (int)((L.hm + BT - 1) / BT);
+  d->tiles_n = (int)((L.hn + BT - 1) / BT);
   d->ksteps = (int)((L.hk + BK - 1) / BK);
   const bool aligned = ((uintptr_t)L.A % 16 == 0) && ((uintptr_t)L.B % 16 == 0) && (L.lda % 2 == 0) &&
                        (L.ldb % 2 == 0) && (L.levels == 0 || (L.hk % 2 == 0 && L.hn % 2 == 0)) &&
                        L.a_cols < (1LL << 31) && L.a_rows < (1LL << 31) && L.b_cols < (1LL << 31) &&
                        L.b_rows < (1LL << 31);
-  d->use_tma = aligned && encode_2d(&d->tmA, L.A, L.a_rows, L.a_cols, L.lda, BK, BM) &&
-               encode_2d(&d->tmB, L.B, L.b_rows, L.b_cols, L.ldb, BN, BK);
+  d->use_tma = aligned && encode_2d(&d->tmA, L.A, L.a_rows, L.a_cols, L.lda, BK, BT) &&
+               encode_2d(&d->tmB, L.B, L.b_rows, L.b_cols, L.ldb, BT, BK);
 }
 
 }  // namespace
@@ -666,28 +687,38 @@ int device_sm_count() {
   return sms;
 }
 
-// Estimated FP64-pipe time (arbitrary units) of a schedule: padded-tile FMAs, operand
-// sums (off the critical path in the producer warps, counted at a quarter) and the
-// wave quantisation of owner scheduling.
-static double estimate(const Fp64Launch& L, int sched, int nprod, int sms) {
-  const double tiles_m = (double)((L.hm + BM - 1) / BM), tiles_n = (double)((L.hn + BN - 1) / BN);
+// Estimated time (FMA-equivalents on the busiest SM) of a launch with a tile and a
+// schedule: every k-step of a tile costs its padded FMAs (64-wide tiles carry a small
+// penalty for their larger share of staging work per FMA) plus a fixed hand-over
+// overhead; stream-K spreads the (unit, k-step) iterations evenly, the owner schedule
+// gives whole tile positions (all products, all of k) to one block each.
+static double estimate(const Fp64Launch& L, int sched, int nprod, int sms, int tile_id) {
+  const int BT = tile_edge(tile_id);
+  const double tiles_m = (double)((L.hm + BT - 1) / BT), tiles_n = (double)((L.hn + BT - 1) / BT);
   const double ksteps = (double)((L.hk + BK - 1) / BK);
-  const double unit = (double)BM * BN * BK * ksteps;
-  if (sched == kSchedStreamK) return unit * nprod * tiles_m * tiles_n / sms;
-  return unit * nprod * std::ceil(tiles_m * tiles_n / sms);
+  const double step = (double)BT * BT * BK * (tile_id == 0 ? 1.0 : kSmallTileFactor) + kStepOverheadFma;
+  if (sched == kSchedStreamK) return step * std::ceil(nprod * tiles_m * tiles_n * ksteps / sms);
+  return step * ksteps * nprod * std::ceil(tiles_m * tiles_n / sms);
+}
+
+int choose_fp64_tile(const Fp64Launch& L, int sms) {
+  const int nprod = L.nprod < 0 ? kPlanCount[L.levels] - L.prod_begin : L.nprod;
+  const double t0 = estimate(L, kSchedStreamK, nprod, sms, 0);
+  const double t1 = estimate(L, kSchedStreamK, nprod, sms, 1);
+  return t1 < t0 ? 1 : 0;
 }
 
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic) {
   int sms = 0;
   ensure_device(&sms);
   if (sms <= 0) sms = 1;
+  if (L->tile < 0 || L->tile >= kTileIds) L->tile = choose_fp64_tile(*L, sms);
   const int nprod = L->nprod < 0 ? kPlanCount[L->levels] - L->prod_begin : L->nprod;
-  const double so = estimate(*L, kSchedOwner, nprod, sms);
-  const double ss = estimate(*L, kSchedStreamK, nprod, sms);
+  const double so = estimate(*L, kSchedOwner, nprod, sms, L->tile);
+  const double ss = estimate(*L, kSchedStreamK, nprod, sms, L->tile);
   // Owner scheduling is deterministic (one writer per C tile, fixed product order):
   // keep it unless stream-K is more than 3% faster by the estimate.
   const bool owner = prefer_deterministic || so <= ss * 1.03;
-  L->tile = 0;
   L->sched = owner ? kSchedOwner : kSchedStreamK;
 }
 
@@ -698,7 +729,9 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream) {
   if (L.levels < 0 || L.levels > kMaxLevels) return cudaErrorInvalidValue;
   KArgs args;
   std::memset(&args, 0, sizeof(args));
-  fill_desc(L, &args.single);
+  Fp64Launch Lt = L;
+  if (Lt.tile < 0 || Lt.tile >= kTileIds) Lt.tile = choose_fp64_tile(Lt, sms);
+  fill_desc(Lt, &args.single);
   const ProbDesc& d = args.single;
   if (d.nprod <= 0 || d.ksteps <= 0 || d.tiles_m <= 0 || d.tiles_n <= 0) return cudaSuccess;
   args.nprob = 1;
@@ -714,8 +747,8 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream) {
   }
   const int cls = term_class_of(L.levels, L.prod_begin, d.nprod);
   void* kargs[] = {&args};
-  return cudaLaunchKernel(pick_kernel(cls, false), dim3((unsigned)grid), dim3(kThreads), kargs, smem_bytes(cls),
-                          stream);
+  return cudaLaunchKernel(pick_kernel(cls, false, Lt.tile), dim3((unsigned)grid), dim3(kThreads), kargs,
+                          smem_bytes(cls, Lt.tile), stream);
 }
 
 // ---------------------------------------------------------------- batched
@@ -762,6 +795,13 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   int sms = 0;
   cudaError_t e = ensure_device(&sms);
   if (e != cudaSuccess) return e;
+  // One tile edge for the whole launch: the one with the smaller summed estimate.
+  double est[kTileIds] = {0.0, 0.0};
+  for (int i = 0; i < count; ++i) {
+    const int nprod = probs[i].nprod < 0 ? kPlanCount[probs[i].levels] - probs[i].prod_begin : probs[i].nprod;
+    for (int t = 0; t < kTileIds; ++t) est[t] += estimate(probs[i], kSchedStreamK, nprod, 1, t);
+  }
+  const int tile = est[1] < est[0] ? 1 : 0;
   std::vector<ProbDesc> descs;
   descs.reserve(count);
   int64_t total = 0;
@@ -771,6 +811,7 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
     Fp64Launch L = probs[i];
     L.epi = kEpiAtomicAdd;
     L.sched = kSchedStreamK;
+    L.tile = tile;
     fill_desc(L, &d);
     if (d.nprod <= 0 || d.ksteps <= 0 || d.tiles_m <= 0 || d.tiles_n <= 0) continue;
     d.iter_begin = total;
@@ -799,8 +840,8 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   args.total = total;
   const int64_t grid = std::min<int64_t>(sms, total);
   void* kargs[] = {&args};
-  return cudaLaunchKernel(pick_kernel(cls, true), dim3((unsigned)grid), dim3(kThreads), kargs, smem_bytes(cls),
-                          stream);
+  return cudaLaunchKernel(pick_kernel(cls, true, tile), dim3((unsigned)grid), dim3(kThreads), kargs,
+                          smem_bytes(cls, tile), stream);
 }
 
 namespace {

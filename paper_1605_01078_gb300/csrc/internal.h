@@ -60,7 +60,7 @@ struct Fp64Launch {
   int m_target;            // 1: every product writes block (0,0) of C with sign + (temporary M)
   EpilogueKind epi;
   ScheduleKind sched;
-  int tile;
+  int tile;                // 0: 128 x 128 block tile, 1: 64 x 64, -1: the library's choice
 };
 
 // Fills the fields common to a full-operand launch.
@@ -85,8 +85,16 @@ cudaError_t launch_wait_timeout_check(long long limit_cycles, cudaStream_t strea
 cudaError_t check_int_fadd(long long count, unsigned long long seed, unsigned long long* mismatches_host,
                            cudaStream_t stream);
 
-// Picks a schedule for a launch (balance heuristics for the SM count).
+// Picks the tile (when L->tile < 0) and the schedule of a launch (balance heuristics
+// for the SM count).
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic);
+
+// Tile edge of a tile id (0: 128, 1: 64) and the number of tile ids.
+constexpr int kNumTiles = 2;
+inline int tile_edge_of(int tile_id) { return tile_id == 0 ? 128 : 64; }
+// Cost of a 64 x 64 tile's multiply-adds relative to a 128 x 128 tile's (its producers
+// stage twice as many source elements per FMA), used by the tile choice and the model.
+constexpr double kSmallTileFactor = 1.03;
 
 // Reads and clears the device-side status word of the product kernels (set when a
 // bounded wait gave up).  Synchronises `stream` first.
@@ -119,8 +127,8 @@ int ozaki_device_status();
 bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate);
 
 // Selection (select.cpp): analytic time model, its argmin, and the exhaustive records.
-double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant);
-void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant);
+double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant, int tile);
+void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant, int* tile);
 bool record_lookup(int64_t m, int64_t n, int64_t k, int dtype, int* levels, int* variant, int* tile);
 void record_store(int64_t m, int64_t n, int64_t k, int dtype, int levels, int variant, int tile);
 void record_clear();

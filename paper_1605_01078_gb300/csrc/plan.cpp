@@ -40,7 +40,7 @@ Fp64Launch make_launch(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   L.m_target = 0;
   L.epi = kEpiAtomicAdd;
   L.sched = kSchedStreamK;
-  L.tile = 0;
+  L.tile = -1;  // chosen by choose_fp64_schedule / launch_fp64
   return L;
 }
 

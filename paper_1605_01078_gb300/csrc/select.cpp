@@ -10,7 +10,7 @@
 //
 // The analytic model restates the paper's T = T_a + T_m for this GPU: T_a counts the
 // FP64 operations the kernels actually execute -- multiply-adds of the padded 128 x 128
-// x 8 tiles (the GPU's analogue of the m_R x n_R micro-tile), the operand-sum and C
+// x 8 or 64 x 64 x 8 tiles (the GPU's analogue of the m_R x n_R micro-tile), the operand-sum and C
 // additions of Naive and AB's separate kernels (the staging sums of ABC and AB run on
 // the integer pipe and cost no FP64 time) -- at the FP64 pipe rate; T_m counts the extra
 // passes of AB and Naive over their temporaries at the HBM rate; and each kernel launch
@@ -32,7 +32,7 @@ constexpr double kAddCost = 1.2;                    // a DADD costs about 1.2 DF
 constexpr double kStageAddCost = 0.0;               // staging sums run on the integer pipe
 constexpr double kBytesPerSec = 6.8e12;             // HBM, measured copy bandwidth
 constexpr double kLaunchSec = 4e-6;
-constexpr int kBM = 128, kBN = 128, kBK = 8;
+constexpr int kBK = 8;
 
 double ceil_to(double x, double q) { return std::ceil(x / q) * q; }
 
@@ -60,12 +60,14 @@ std::unordered_map<Key, Choice, KeyHash> g_records;
 
 }  // namespace
 
-double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant) {
+double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant, int tile) {
   Plan pl;
-  if (!make_plan(levels, &pl)) return 1e30;
+  if (!make_plan(levels, &pl) || tile < 0 || tile >= kNumTiles) return 1e30;
+  const double edge = (double)tile_edge_of(tile);
   const double hm = (double)block_edge(m, levels), hn = (double)block_edge(n, levels),
                hk = (double)block_edge(k, levels);
-  const double pm = ceil_to(hm, kBM), pn = ceil_to(hn, kBN), pk = ceil_to(hk, kBK);
+  const double pm = ceil_to(hm, edge), pn = ceil_to(hn, edge), pk = ceil_to(hk, kBK);
+  const double tile_factor = tile == 0 ? 1.0 : kSmallTileFactor;
   double fma = 0, adds = 0, bytes = 0, launches = 0;
   if (levels == 0) {
     fma = pm * pn * pk;
@@ -76,7 +78,7 @@ double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant) {
     for (int r = 0; r < pl.nprod; ++r) {
       fma += pm * pn * pk;
       adds += kStageAddCost / kAddCost * pm * pn * pk *
-              ((pl.na[r] - 1) / (double)kBN + (pl.nb[r] - 1) / (double)kBM);
+              ((pl.na[r] - 1) / edge + (pl.nb[r] - 1) / edge);
     }
     if (variant == STRASSEN_ABC) {
       launches = 1;
@@ -95,25 +97,37 @@ double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant) {
     }
     launches = 5.0 * pl.nprod;
   }
-  return (fma + kAddCost * adds) / kFmaPerSec + bytes / kBytesPerSec + launches * kLaunchSec;
+  return (tile_factor * fma + kAddCost * adds) / kFmaPerSec + bytes / kBytesPerSec + launches * kLaunchSec;
 }
 
-void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant) {
-  double best = model_seconds(m, n, k, 0, STRASSEN_ABC);
+void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant, int* tile) {
+  auto best_tile = [&](int L, int v, int* t_out) {
+    double b = 1e300;
+    for (int t = 0; t < kNumTiles; ++t) {
+      const double x = model_seconds(m, n, k, L, v, t);
+      if (x < b) { b = x; *t_out = t; }
+    }
+    return b;
+  };
+  int bt = 0;
+  double best = best_tile(0, STRASSEN_ABC, &bt);
   int bl = 0, bv = STRASSEN_ABC;
   for (int L = 1; L <= kMaxLevels; ++L) {
     if (((int64_t)1 << L) > m || ((int64_t)1 << L) > n || ((int64_t)1 << L) > k) break;
     for (int v : {STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE}) {
-      const double t = model_seconds(m, n, k, L, v);
-      if (t < best * 0.99) {  // prefer fewer levels / ABC within 1%
-        best = t;
+      int t = 0;
+      const double x = best_tile(L, v, &t);
+      if (x < best * 0.99) {  // prefer fewer levels / ABC within 1%
+        best = x;
         bl = L;
         bv = v;
+        bt = t;
       }
     }
   }
   *levels = bl;
   *variant = bv;
+  *tile = bt;
 }
 
 bool record_lookup(int64_t m, int64_t n, int64_t k, int dtype, int* levels, int* variant, int* tile) {

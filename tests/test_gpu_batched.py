@@ -44,6 +44,24 @@ def test_batched_integer_bit_exact_mixed_levels():
         assert np.array_equal(dC.cpu().numpy(), ref), (tuple(dA.shape), tuple(dB.shape), lv)
 
 
+def test_batched_large_aligned_problems_bit_exact():
+    """Large tile-aligned problems (the launch takes the 128-wide tile) mixed over
+    levels 0..3, integer inputs: bit for bit against the oracle."""
+    shapes = [(1536, 1024, 512), (1024, 1536, 768), (2048, 1024, 256), (1024, 1024, 1024)]
+    items, host = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, B, C = W.integer(m, k, 70 + i), W.integer(k, n, 80 + i), W.integer(m, n, 90 + i)
+        ref = C.copy()
+        oracle.gemm(A, B, ref)
+        items.append(tuple(torch.from_numpy(x).cuda() for x in (A, B, C)) + (i, sg.STRASSEN_ABC))
+        host.append(ref)
+    arr = problems_array(items)
+    assert sg.strassen_gemm_batched(len(items), arr, sg.STRASSEN_F64, torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    for it, ref in zip(items, host):
+        assert np.array_equal(it[2].cpu().numpy(), ref)
+
+
 def test_batched_rejects_overlapping_outputs_and_bad_problems():
     A = torch.zeros((8, 8), dtype=torch.float64, device="cuda")
     B = torch.zeros((8, 8), dtype=torch.float64, device="cuda")

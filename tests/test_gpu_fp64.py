@@ -224,3 +224,46 @@ def test_full_size_sampled_against_dot2(levels, variant):
     else:
         # elementwise error stays within the strict max-norm tolerance scaled by k
         assert float(np.max(np.abs(got - ref))) <= TOL[levels] * n
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("levels,variant", [(0, "ABC"), (1, "AB"), (2, "ABC"), (2, "NAIVE"), (3, "ABC")])
+def test_both_block_tiles_bit_exact(tile, levels, variant):
+    """Both block tiles (0: 128 x 128, 1: 64 x 64) on the same ragged shape: an
+    exhaustive-measurement record fixes (levels, variant, tile) and the automatic call
+    follows it; integer inputs must match the oracle bit for bit."""
+    m, n, k = 333, 290, 517
+    A, B, C = W.integer(m, k, 41), W.integer(k, n, 42), W.integer(m, n, 43)
+    ref = ref_gemm(A, B, C)
+    v = {"ABC": sg.STRASSEN_ABC, "AB": sg.STRASSEN_AB, "NAIVE": sg.STRASSEN_NAIVE}[variant]
+    assert sg.strassen_tune_record(m, n, k, sg.STRASSEN_F64, levels, v, tile) == 0
+    try:
+        assert sg.strassen_select(m, n, k, sg.STRASSEN_F64) == (levels, v, tile)
+        dC = dev(C)
+        sg.gemm(dev(A), dev(B), dC, levels=-1, variant="AUTO")
+        torch.cuda.synchronize()
+        assert np.array_equal(dC.cpu().numpy(), ref)
+    finally:
+        sg.strassen_tune_clear()
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+def test_both_block_tiles_float_tolerance(tile):
+    case = float_case(255, 333, 517, 7, 8, 9, False)
+    m, k = case[0].shape
+    n = case[1].shape[1]
+    assert sg.strassen_tune_record(m, n, k, sg.STRASSEN_F64, 2, sg.STRASSEN_ABC, tile) == 0
+    try:
+        dC = dev(case[2])
+        sg.gemm(dev(case[0]), dev(case[1]), dC, levels=-1, variant="AUTO")
+        torch.cuda.synchronize()
+        check_float(dC.cpu().numpy(), 2, case)
+    finally:
+        sg.strassen_tune_clear()
+
+
+def test_tile_choice_follows_padding():
+    """The model picks the 64-wide tile where 128-wide tiles would mostly compute
+    padding, and the 128-wide tile for large aligned blocks."""
+    assert sg.strassen_select(300, 280, 2000, sg.STRASSEN_F64)[2] == 1
+    assert sg.strassen_select(8192, 8192, 8192, sg.STRASSEN_F64)[2] == 0
