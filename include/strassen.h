@@ -156,9 +156,12 @@ typedef struct {
  *   count   number of problems (>= 0).
  *   probs   HOST array of `count` problems; each is validated as in strassen_gemm.
  *           The byte ranges [C, C + (m-1)*ldc + n) of different problems must not
- *           overlap (STRASSEN_ERR_ARG otherwise).  levels = -1 or variant =
- *           STRASSEN_AUTO takes strassen_select()'s level; every problem runs as ABC
- *           (levels 1-3) or classical (levels 0) inside the one launch.
+ *           overlap (STRASSEN_ERR_ARG otherwise).  Every problem runs as ABC
+ *           (levels 1-3) or classical (levels 0) inside the one launch, and the
+ *           launch uses one block tile (128x128 or 64x64) for all of them.  levels =
+ *           -1 takes an exhaustive record for the shape (strassen_tune_record) if
+ *           there is one; otherwise the level is chosen together with the launch's
+ *           tile, minimising the summed estimate of padded tile work.
  *   dtype   STRASSEN_F64.
  *   stream  the CUDA stream.
  *

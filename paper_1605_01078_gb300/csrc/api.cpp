@@ -224,6 +224,7 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
     if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
     if (dtype != STRASSEN_F64) return STRASSEN_ERR_UNSUPPORTED;
     std::vector<Fp64Launch> launches;
+    std::vector<char> free_levels;  // 1: the level is chosen below, jointly with the tile
     std::vector<std::pair<const char*, const char*>> cranges;
     launches.reserve(count);
     for (int i = 0; i < count; ++i) {
@@ -234,18 +235,53 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
       if (chk < 0) return chk;
       if (chk == 1) continue;
       int levels = p.levels;
-      if (levels == -1 || p.variant == STRASSEN_AUTO) {
-        int sl = 0, tile = 0;
-        strassen_variant sv = STRASSEN_ABC;
-        const int st = strassen_select(p.m, p.n, p.k, dtype, &sl, &sv, &tile);
-        if (st != STRASSEN_OK) return st;
-        if (levels == -1) levels = sl;
+      bool chosen_here = false;
+      if (levels == -1) {
+        int rl = 0, rv = 0, rt = 0;
+        if (record_lookup(p.m, p.n, p.k, (int)dtype, &rl, &rv, &rt)) levels = rl;  // exhaustive record
+        else chosen_here = true;
       }
-      levels = clamp_levels(levels, p.m, p.n, p.k);
+      levels = chosen_here ? 0 : clamp_levels(levels, p.m, p.n, p.k);
       launches.push_back(make_launch(p.m, p.n, p.k, p.A, p.lda, p.B, p.ldb, p.C, p.ldc, levels));
+      free_levels.push_back(chosen_here ? 1 : 0);
       cranges.emplace_back((const char*)p.C, (const char*)(p.C + (p.m - 1) * p.ldc + p.n));
     }
     if (launches.empty()) return STRASSEN_OK;
+    // One launch runs every problem with one block tile, so the automatic levels are
+    // chosen together with it: for each tile, every free problem takes the level with
+    // the smallest estimate under that tile, and the tile with the smallest total wins.
+    {
+      const int sms = std::max(device_sm_count(), 1);
+      std::vector<int> best_level[kNumTiles];
+      double total[kNumTiles] = {0.0, 0.0};
+      for (int t = 0; t < kNumTiles; ++t) {
+        best_level[t].assign(launches.size(), 0);
+        for (size_t i = 0; i < launches.size(); ++i) {
+          const Fp64Launch& L = launches[i];
+          if (!free_levels[i]) {
+            total[t] += fp64_launch_estimate(L, t, sms);
+            continue;
+          }
+          const int64_t m = L.a_rows, k = L.a_cols, n = L.b_cols;
+          double b = 1e300;
+          for (int lv = 0; lv <= clamp_levels(kMaxLevels, m, n, k); ++lv) {
+            const Fp64Launch Lv = make_launch(m, n, k, L.A, L.lda, L.B, L.ldb, L.C, L.ldc, lv);
+            const double x = fp64_launch_estimate(Lv, t, sms);
+            if (x < b * 0.99) { b = x; best_level[t][i] = lv; }  // fewer levels within 1 %
+          }
+          total[t] += b;
+        }
+      }
+      const int tile = total[1] < total[0] ? 1 : 0;
+      for (size_t i = 0; i < launches.size(); ++i) {
+        if (free_levels[i]) {
+          const Fp64Launch& L = launches[i];
+          launches[i] = make_launch(L.a_rows, L.b_cols, L.a_cols, L.A, L.lda, L.B, L.ldb, L.C, L.ldc,
+                                    best_level[tile][i]);
+        }
+        launches[i].tile = tile;
+      }
+    }
     // The C ranges of different problems must not overlap (atomics would mix them).
     std::sort(cranges.begin(), cranges.end());
     for (size_t i = 1; i < cranges.size(); ++i)

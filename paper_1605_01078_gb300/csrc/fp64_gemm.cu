@@ -696,12 +696,17 @@ static double estimate(const Fp64Launch& L, int sched, int nprod, int sms, int t
   const int BT = tile_edge(tile_id);
   const double tiles_m = (double)((L.hm + BT - 1) / BT), tiles_n = (double)((L.hn + BT - 1) / BT);
   const double ksteps = (double)((L.hk + BK - 1) / BK);
-  const double step = (double)BT * BT * BK * (tile_id == 0 ? 1.0 : kSmallTileFactor) + kStepOverheadFma;
+  const double step = (double)BT * BT * BK * (tile_id == 0 ? 1.0 : small_tile_factor(L.levels)) + kStepOverheadFma;
   if (sched == kSchedStreamK) return step * std::ceil(nprod * tiles_m * tiles_n * ksteps / sms);
   return step * ksteps * nprod * std::ceil(tiles_m * tiles_n / sms);
 }
 
-int choose_fp64_tile(const Fp64Launch& L, int sms) {
+double fp64_launch_estimate(const Fp64Launch& L, int tile_id, int sms) {
+  const int nprod = L.nprod < 0 ? kPlanCount[L.levels] - L.prod_begin : L.nprod;
+  return estimate(L, kSchedStreamK, nprod, sms, tile_id);
+}
+
+static int choose_fp64_tile(const Fp64Launch& L, int sms) {
   const int nprod = L.nprod < 0 ? kPlanCount[L.levels] - L.prod_begin : L.nprod;
   const double t0 = estimate(L, kSchedStreamK, nprod, sms, 0);
   const double t1 = estimate(L, kSchedStreamK, nprod, sms, 1);
@@ -795,13 +800,17 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   int sms = 0;
   cudaError_t e = ensure_device(&sms);
   if (e != cudaSuccess) return e;
-  // One tile edge for the whole launch: the one with the smaller summed estimate.
-  double est[kTileIds] = {0.0, 0.0};
-  for (int i = 0; i < count; ++i) {
-    const int nprod = probs[i].nprod < 0 ? kPlanCount[probs[i].levels] - probs[i].prod_begin : probs[i].nprod;
-    for (int t = 0; t < kTileIds; ++t) est[t] += estimate(probs[i], kSchedStreamK, nprod, 1, t);
+  // One tile edge for the whole launch: the callers' choice when they agree, else the
+  // one with the smaller summed estimate.
+  int tile = probs[0].tile;
+  for (int i = 1; i < count; ++i)
+    if (probs[i].tile != tile) tile = -1;
+  if (tile < 0 || tile >= kTileIds) {
+    double est[kTileIds] = {0.0, 0.0};
+    for (int i = 0; i < count; ++i)
+      for (int t = 0; t < kTileIds; ++t) est[t] += fp64_launch_estimate(probs[i], t, 1);
+    tile = est[1] < est[0] ? 1 : 0;
   }
-  const int tile = est[1] < est[0] ? 1 : 0;
   std::vector<ProbDesc> descs;
   descs.reserve(count);
   int64_t total = 0;

@@ -75,6 +75,10 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream);
 size_t fp64_batched_scratch_bytes(int count);
 cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratch, cudaStream_t stream);
 
+// Estimated busiest-SM time (FMA-equivalents) of one problem under a tile id and the
+// stream-K schedule on `sms` blocks: the quantity the tile choices minimise.
+double fp64_launch_estimate(const Fp64Launch& L, int tile_id, int sms);
+
 // Launches one thread that waits on an mbarrier nothing completes, for `limit_cycles`
 // clock cycles: exercises the bounded-wait path (the status word becomes
 // STRASSEN_ERR_TIMEOUT and the kernel returns).
@@ -92,9 +96,11 @@ void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic);
 // Tile edge of a tile id (0: 128, 1: 64) and the number of tile ids.
 constexpr int kNumTiles = 2;
 inline int tile_edge_of(int tile_id) { return tile_id == 0 ? 128 : 64; }
-// Cost of a 64 x 64 tile's multiply-adds relative to a 128 x 128 tile's (its producers
-// stage twice as many source elements per FMA), used by the tile choice and the model.
-constexpr double kSmallTileFactor = 1.03;
+// Cost of a 64 x 64 tile's multiply-adds relative to a 128 x 128 tile's, used by the
+// tile choice and the model.  Its producers stage twice as many source elements per
+// FMA: invisible up to two levels (measured 1.00-1.01), but the up-to-eight-term sums
+// of three levels make the producers the bottleneck (measured 1.24).
+inline double small_tile_factor(int levels) { return levels >= 3 ? 1.24 : 1.01; }
 
 // Reads and clears the device-side status word of the product kernels (set when a
 // bounded wait gave up).  Synchronises `stream` first.

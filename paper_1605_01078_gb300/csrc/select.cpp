@@ -67,7 +67,7 @@ double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant, i
   const double hm = (double)block_edge(m, levels), hn = (double)block_edge(n, levels),
                hk = (double)block_edge(k, levels);
   const double pm = ceil_to(hm, edge), pn = ceil_to(hn, edge), pk = ceil_to(hk, kBK);
-  const double tile_factor = tile == 0 ? 1.0 : kSmallTileFactor;
+  const double tile_factor = tile == 0 ? 1.0 : small_tile_factor(levels);
   double fma = 0, adds = 0, bytes = 0, launches = 0;
   if (levels == 0) {
     fma = pm * pn * pk;
