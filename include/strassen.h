@@ -150,18 +150,19 @@ typedef struct {
 } strassen_problem;
 
 /*
- * strassen_gemm_batched -- many independent products of uneven shapes in ONE
- * persistent kernel launch (the batching pattern; not in the paper).
+ * strassen_gemm_batched -- many independent products of uneven shapes in one
+ * persistent kernel launch per block tile (the batching pattern; not in the paper).
  *
  *   count   number of problems (>= 0).
  *   probs   HOST array of `count` problems; each is validated as in strassen_gemm.
  *           The byte ranges [C, C + (m-1)*ldc + n) of different problems must not
  *           overlap (STRASSEN_ERR_ARG otherwise).  Every problem runs as ABC
- *           (levels 1-3) or classical (levels 0) inside the one launch, and the
- *           launch uses one block tile (128x128 or 64x64) for all of them.  levels =
- *           -1 takes an exhaustive record for the shape (strassen_tune_record) if
- *           there is one; otherwise the level is chosen together with the launch's
- *           tile, minimising the summed estimate of padded tile work.
+ *           (levels 1-3) or classical (levels 0).  Each problem gets the block tile
+ *           (128x128 or 64x64) with the smaller estimate of padded tile work, and
+ *           with levels = -1 also the level (an exhaustive record for the shape,
+ *           strassen_tune_record, takes precedence).  The problems of one tile share
+ *           one persistent launch: the call makes one launch per tile in use (at
+ *           most two).
  *   dtype   STRASSEN_F64.
  *   stream  the CUDA stream.
  *

@@ -247,40 +247,25 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
       cranges.emplace_back((const char*)p.C, (const char*)(p.C + (p.m - 1) * p.ldc + p.n));
     }
     if (launches.empty()) return STRASSEN_OK;
-    // One launch runs every problem with one block tile, so the automatic levels are
-    // chosen together with it: for each tile, every free problem takes the level with
-    // the smallest estimate under that tile, and the tile with the smallest total wins.
-    {
-      const int sms = std::max(device_sm_count(), 1);
-      std::vector<int> best_level[kNumTiles];
-      double total[kNumTiles] = {0.0, 0.0};
-      for (int t = 0; t < kNumTiles; ++t) {
-        best_level[t].assign(launches.size(), 0);
-        for (size_t i = 0; i < launches.size(); ++i) {
-          const Fp64Launch& L = launches[i];
-          if (!free_levels[i]) {
-            total[t] += fp64_launch_estimate(L, t, sms);
-            continue;
-          }
-          const int64_t m = L.a_rows, k = L.a_cols, n = L.b_cols;
-          double b = 1e300;
-          for (int lv = 0; lv <= clamp_levels(kMaxLevels, m, n, k); ++lv) {
-            const Fp64Launch Lv = make_launch(m, n, k, L.A, L.lda, L.B, L.ldb, L.C, L.ldc, lv);
-            const double x = fp64_launch_estimate(Lv, t, sms);
-            if (x < b * 0.99) { b = x; best_level[t][i] = lv; }  // fewer levels within 1 %
-          }
-          total[t] += b;
+    // Each problem takes the block tile (and, when free, the level) with the smallest
+    // estimate of its padded tile work; the problems of one tile share one persistent
+    // launch, so the call makes one launch per tile in use (at most two).
+    for (size_t i = 0; i < launches.size(); ++i) {
+      const Fp64Launch L = launches[i];
+      const int64_t m = L.a_rows, k = L.a_cols, n = L.b_cols;
+      const int lv_hi = free_levels[i] ? clamp_levels(kMaxLevels, m, n, k) : L.levels;
+      const int lv_lo = free_levels[i] ? 0 : L.levels;
+      double b = 1e300;
+      int bl = L.levels, bt = 0;
+      for (int lv = lv_lo; lv <= lv_hi; ++lv) {
+        const Fp64Launch Lv = make_launch(m, n, k, L.A, L.lda, L.B, L.ldb, L.C, L.ldc, lv);
+        for (int t = 0; t < kNumTiles; ++t) {
+          const double x = fp64_launch_estimate(Lv, t, 1);
+          if (x < b * 0.99) { b = x; bl = lv; bt = t; }  // fewer levels, then the larger tile, within 1 %
         }
       }
-      const int tile = total[1] < total[0] ? 1 : 0;
-      for (size_t i = 0; i < launches.size(); ++i) {
-        if (free_levels[i]) {
-          const Fp64Launch& L = launches[i];
-          launches[i] = make_launch(L.a_rows, L.b_cols, L.a_cols, L.A, L.lda, L.B, L.ldb, L.C, L.ldc,
-                                    best_level[tile][i]);
-        }
-        launches[i].tile = tile;
-      }
+      launches[i] = make_launch(m, n, k, L.A, L.lda, L.B, L.ldb, L.C, L.ldc, bl);
+      launches[i].tile = bt;
     }
     // The C ranges of different problems must not overlap (atomics would mix them).
     std::sort(cranges.begin(), cranges.end());
@@ -293,12 +278,24 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
     }
     Workspace ws;
     ws.s = s;
-    if (cudaMallocAsync(&ws.p, fp64_batched_scratch_bytes((int)launches.size()), s) != cudaSuccess) {
+    if (cudaMallocAsync(&ws.p, 2 * fp64_batched_scratch_bytes((int)launches.size()), s) != cudaSuccess) {
       cudaGetLastError();
       ws.p = nullptr;
       return STRASSEN_ERR_ALLOC;
     }
-    return cuda_status(launch_fp64_batched(launches.data(), (int)launches.size(), ws.p, s));
+    std::stable_partition(launches.begin(), launches.end(), [](const Fp64Launch& L) { return L.tile == 0; });
+    const size_t n0 = (size_t)std::count_if(launches.begin(), launches.end(),
+                                            [](const Fp64Launch& L) { return L.tile == 0; });
+    if (n0 > 0) {
+      const cudaError_t e = launch_fp64_batched(launches.data(), (int)n0, ws.p, s);
+      if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    }
+    if (n0 < launches.size()) {
+      void* scratch1 = (char*)ws.p + fp64_batched_scratch_bytes((int)n0);
+      const cudaError_t e = launch_fp64_batched(launches.data() + n0, (int)(launches.size() - n0), scratch1, s);
+      if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    }
+    return STRASSEN_OK;
   } catch (...) {
     return STRASSEN_ERR_ALLOC;
   }
