@@ -79,7 +79,7 @@ constexpr long long kWaitLimitCycles = 2000000000LL;  // ~1 s at 2 GHz
 // the producer warpgroup gives registers back and the two consumer warpgroups take
 // them.  The shares add up exactly to the launch total, so the increase never waits
 // on registers that do not exist.
-constexpr int kLaunchRegs = 168, kProducerRegs = 72, kConsumerRegs = 216;
+constexpr int kLaunchRegs = 168, kProducerRegs = 88, kConsumerRegs = 208;
 static_assert(kProducers * kProducerRegs + kConsumers * kConsumerRegs == kThreads * kLaunchRegs,
               "register split must add up to the launch allocation");
 
@@ -103,10 +103,20 @@ struct alignas(128) ProbDesc {
 struct KArgs {
   ProbDesc single;         // the problem when not batched
   const ProbDesc* descs;   // device array when batched
+  unsigned long long* chunk_counter;  // batched: next chunk to claim (cleared before the launch)
   int nprob;
   int sched;
   int64_t total;           // stream-K: iterations of all problems; owner: tile positions
+  int64_t chunk;           // batched: iterations per claimed chunk
+  int64_t nchunks;
 };
+
+// What the producers tell the consumers about the k-step in a summed slot.
+struct StepMeta {
+  int p, r, t;  // problem, product, tile of the step
+  int flags;    // kStepLast: the last k-step of this block's part of the unit; kStepEnd: no step
+};
+constexpr int kStepLast = 1, kStepEnd = 2;
 
 template <int MAXT, int BT>
 struct Smem {
@@ -116,7 +126,7 @@ struct Smem {
   static constexpr int kRawB = MAXT * BK * BN;
   static constexpr size_t kBytes =
       sizeof(double) * (size_t)(NR * (kRawA + kRawB) + NS * BK * (BM + BN) + (kConsumers / 32) * 2 * BN) +
-      sizeof(uint64_t) * (2 * NR + 2 * NS);
+      sizeof(uint64_t) * (2 * NR + 2 * NS) + sizeof(StepMeta) * NS + 16;
   static_assert(kBytes <= 227 * 1024, "shared memory per block");
 };
 
@@ -187,13 +197,22 @@ __device__ __forceinline__ const ProbDesc& desc_of(const KArgs& a, int p) {
   else return a.single;
 }
 
+// Cursor on range `id` of the work: batched launches claim chunks of `chunk`
+// iterations of the stream-K space; single launches have one range per block (a
+// stream-K share, or the block's tile positions under the owner schedule).
 template <bool BATCHED>
-__device__ Cursor cursor_begin(const KArgs& a, int64_t* count_out) {
+__device__ Cursor range_cursor(const KArgs& a, int64_t id) {
   Cursor c;
   c.p = 0; c.r = 0; c.t = 0; c.ks = 0; c.left = 0;
-  if (a.sched == kSchedStreamK) {
-    const int64_t beg = (a.total * (int64_t)blockIdx.x) / gridDim.x;
-    const int64_t end = (a.total * (int64_t)(blockIdx.x + 1)) / gridDim.x;
+  if (BATCHED || a.sched == kSchedStreamK) {
+    int64_t beg, end;
+    if constexpr (BATCHED) {
+      beg = id * a.chunk;
+      end = beg + a.chunk < a.total ? beg + a.chunk : a.total;
+    } else {
+      beg = (a.total * id) / gridDim.x;
+      end = (a.total * (id + 1)) / gridDim.x;
+    }
     c.left = end - beg;
     if (c.left > 0) {
       int p = 0;
@@ -216,18 +235,17 @@ __device__ Cursor cursor_begin(const KArgs& a, int64_t* count_out) {
     }
   } else {
     const ProbDesc& d = desc_of<BATCHED>(a, 0);
-    const int64_t owned = (a.total > blockIdx.x) ? (a.total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t owned = (a.total > id) ? (a.total - 1 - id) / gridDim.x + 1 : 0;
     c.left = owned * d.nprod * d.ksteps;
-    c.t = blockIdx.x;
+    c.t = (int)id;
   }
-  *count_out = c.left;
   return c;
 }
 
 template <bool BATCHED>
 __device__ __forceinline__ bool cursor_last(const KArgs& a, const Cursor& c) {
   const ProbDesc& d = desc_of<BATCHED>(a, c.p);
-  return c.ks == d.ksteps - 1 || (a.sched == kSchedStreamK && c.left == 1);
+  return c.ks == d.ksteps - 1 || ((BATCHED || a.sched == kSchedStreamK) && c.left == 1);
 }
 
 template <bool BATCHED>
@@ -236,7 +254,7 @@ __device__ __forceinline__ void cursor_next(const KArgs& a, Cursor& c) {
   --c.left;
   if (++c.ks < d.ksteps) return;
   c.ks = 0;
-  if (a.sched == kSchedStreamK) {
+  if (BATCHED || a.sched == kSchedStreamK) {
     if (++c.t < d.tiles_m * d.tiles_n) return;
     c.t = 0;
     if (++c.r < d.nprod) return;
@@ -267,11 +285,17 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
   uint64_t* raw_empty = bars + NR;        // count kProducers
   uint64_t* sum_full = bars + 2 * NR;     // count kProducers
   uint64_t* sum_empty = bars + 2 * NR + NS;  // count kConsumers
+  StepMeta* meta = reinterpret_cast<StepMeta*>(bars + 2 * NR + 2 * NS);  // [NS], written by producer 0
+  uint64_t* claim_full = reinterpret_cast<uint64_t*>(meta + NS);          // count 1
+  uint64_t* claim_empty = claim_full + 1;                                 // count kProducers - 1
+  unsigned long long* claim_slot = reinterpret_cast<unsigned long long*>(claim_full + 2);
 
   const int tid = threadIdx.x;
   if (tid == 0) {
     for (int i = 0; i < NR; ++i) { mbar_init(&raw_full[i], kProducers); mbar_init(&raw_empty[i], kProducers); }
     for (int i = 0; i < NS; ++i) { mbar_init(&sum_full[i], kProducers); mbar_init(&sum_empty[i], kConsumers); }
+    mbar_init(claim_full, 1);
+    mbar_init(claim_empty, kProducers - 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
@@ -288,15 +312,50 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
   }
   __syncthreads();
 
-  int64_t count = 0;
-  Cursor cur = cursor_begin<BATCHED>(a, &count);
-  if (count <= 0) return;
+  Cursor cur;  // the producers' sum cursor
+  cur.p = 0; cur.r = 0; cur.t = 0; cur.ks = 0; cur.left = 0;
 
   if (tid >= kConsumers) {
     // ======================= producers =======================
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kProducerRegs));
     const int pt = tid - kConsumers;
-    Cursor cl = cur;  // load cursor (one step ahead of the sum cursor)
+    Cursor cl = cur;  // load cursor (NR - 1 steps ahead of the sum cursor)
+    bool timed_out = false;
+    // Ranges of the work this block claims: a single launch has one per block; a
+    // batched launch claims chunks from a global counter until none are left, so blocks
+    // that meet cheaper iterations simply take more chunks.  Producer 0 claims and
+    // hands the id to the other producers through shared memory (bounded waits on two
+    // mbarriers).  The load cursor claims; the sum cursor follows through a two-entry
+    // queue (the load cursor runs at most one step, so at most one range, ahead).
+    int64_t fifo[2] = {0, 0};
+    int fin = 0, fout = 0, nclaims = 0;
+    bool claims_done = false;
+    auto claim = [&]() -> int64_t {
+      if constexpr (BATCHED) {
+        if (pt == 0) {
+          if (nclaims > 0 && !mbar_wait(claim_empty, (uint32_t)((nclaims - 1) & 1))) { timed_out = true; return -1; }
+          *claim_slot = atomicAdd(a.chunk_counter, 1ULL);
+          mbar_arrive(claim_full);
+        }
+        if (!mbar_wait(claim_full, (uint32_t)(nclaims & 1))) { timed_out = true; return -1; }
+        const unsigned long long c = *claim_slot;
+        if (pt != 0) mbar_arrive(claim_empty);
+        ++nclaims;
+        return c < (unsigned long long)a.nchunks ? (int64_t)c : -1;
+      } else {
+        return nclaims++ == 0 ? (int64_t)blockIdx.x : -1;
+      }
+    };
+    auto advance_load = [&]() -> bool {
+      while (cl.left <= 0) {
+        if (claims_done || timed_out) return false;
+        const int64_t id = claim();
+        if (id < 0) { claims_done = true; return false; }
+        cl = range_cursor<BATCHED>(a, id);
+        if (cl.left > 0) fifo[(fin++) & 1] = id;
+      }
+      return true;
+    };
 
     auto issue = [&](const Cursor& c, int slot) {
       const ProbDesc& d = desc_of<BATCHED>(a, c.p);
@@ -356,15 +415,15 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
     // slot that step s - 1 has released.
     constexpr int kAhead = NR - 1;
     int64_t issued = 0, landed = 0;
-    for (; issued < kAhead && issued < count; ++issued) {
+    for (; issued < kAhead && advance_load(); ++issued) {
       issue(cl, (int)issued);
       cursor_next<BATCHED>(a, cl);
     }
-    bool timed_out = false;
-    for (int64_t s = 0; s < count && !timed_out; ++s) {
-      if (s + kAhead < count) {
-        const int slot1 = (int)((s + kAhead) % NR);
-        const int64_t use1 = (s + kAhead) / NR;
+    int64_t s = 0;
+    for (; !timed_out; ++s) {
+      if (advance_load()) {
+        const int slot1 = (int)(issued % NR);
+        const int64_t use1 = issued / NR;
         if (use1 > 0 && !mbar_wait(&raw_empty[slot1], (uint32_t)((use1 - 1) & 1))) {
           timed_out = true;
           break;
@@ -373,6 +432,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
         ++issued;
         cursor_next<BATCHED>(a, cl);
       }
+      if (timed_out || s >= issued) break;  // no step s: this block's work is done
+      if (cur.left <= 0) cur = range_cursor<BATCHED>(a, fifo[(fout++) & 1]);
       const int slot = (int)(s % NR);
       const int q = (int)(s % NS);
       if (!mbar_wait(&raw_full[slot], (uint32_t)((s / NR) & 1))) {
@@ -439,9 +500,20 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
         for (int i = 0; i < EPT; ++i) sb[(koff + i) * BN + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
       }
+      if (pt == 0) meta[q] = StepMeta{cur.p, cur.r, cur.t, cursor_last<BATCHED>(a, cur) ? kStepLast : 0};
       mbar_arrive(&sum_full[q]);
       mbar_arrive(&raw_empty[slot]);
       cursor_next<BATCHED>(a, cur);
+    }
+    if (!timed_out) {
+      // End marker for the consumers in the next summed slot.
+      const int q = (int)(s % NS);
+      if (s >= NS && !mbar_wait(&sum_empty[q], (uint32_t)(((s / NS) - 1) & 1))) {
+        timed_out = true;
+      } else {
+        if (pt == 0) meta[q] = StepMeta{0, 0, 0, kStepEnd};
+        mbar_arrive(&sum_full[q]);
+      }
     }
     if (timed_out) {
       record_timeout();
@@ -461,12 +533,13 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
-  for (int64_t s = 0; s < count; ++s) {
+  for (int64_t s = 0;; ++s) {
     const int q = (int)(s % NS);
     if (!mbar_wait(&sum_full[q], (uint32_t)((s / NS) & 1))) {
       record_timeout();
       return;
     }
+    if (meta[q].flags & kStepEnd) break;
     const double* sa = sumA + q * BK * BM;
     const double* sb = sumB + q * BK * BN;
     // One k at a time: 64 independent FMAs per k already cover the FP64 pipe's
@@ -495,17 +568,20 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
     }
+    // The step's metadata is read after the multiply-adds (it holds no registers
+    // during them) and before the slot is released.
+    const StepMeta m = meta[q];
     mbar_arrive(&sum_empty[q]);
 
-    if (cursor_last<BATCHED>(a, cur)) {
+    if (m.flags & kStepLast) {
       // Scatter epilogue: C_q += gamma_q * M_tile for every target of the product.
       // The tile leaves the registers one row group at a time through a per-warp
       // staging buffer, so that each warp issues coalesced atomics over whole tile rows
       // (and the register tile is not held twice).
-      const ProbDesc& d = desc_of<BATCHED>(a, cur.p);
-      const int row = d.plan_row + cur.r;
+      const ProbDesc& d = desc_of<BATCHED>(a, m.p);
+      const int row = d.plan_row + m.r;
       const int nc = d.m_target ? 1 : (int)c_plans.nc[row];
-      const int tm = cur.t / d.tiles_n, tn = cur.t - (cur.t / d.tiles_n) * d.tiles_n;
+      const int tm = m.t / d.tiles_n, tn = m.t - (m.t / d.tiles_n) * d.tiles_n;
       const int warp = tid >> 5, lane = tid & 31;
       double* stage = epi_stage + warp * (2 * BN);
       const int half = ty - 2 * warp;  // which of the warp's two thread rows
@@ -549,7 +625,6 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
     }
-    cursor_next<BATCHED>(a, cur);
   }
 }
 
@@ -765,13 +840,16 @@ namespace {
 // descriptors -- TMA tensor maps encoded on the host included -- into the device
 // array the persistent kernel reads.
 constexpr int kDescPerExpand = (32000 - 64) / (int)sizeof(ProbDesc);
+constexpr int kChunksPerBlock = 16;
 struct ExpandArgs {
   ProbDesc* out;
+  unsigned long long* counter;  // cleared when not null
   int count;
   ProbDesc d[kDescPerExpand];
 };
 
 __global__ void expand_batch_kernel(const __grid_constant__ ExpandArgs a) {
+  if (a.counter != nullptr && threadIdx.x == 0) *a.counter = 0ULL;
   const int words = (int)(sizeof(ProbDesc) / sizeof(uint4));
   for (int w = threadIdx.x; w < a.count * words; w += blockDim.x) {
     const int i = w / words, o = w - (w / words) * words;
@@ -794,7 +872,8 @@ __global__ void wait_timeout_check_kernel(long long limit) {
 
 }  // namespace
 
-size_t fp64_batched_scratch_bytes(int count) { return sizeof(ProbDesc) * (size_t)std::max(count, 1); }
+// Descriptors, then the chunk counter.
+size_t fp64_batched_scratch_bytes(int count) { return sizeof(ProbDesc) * (size_t)std::max(count, 1) + 256; }
 
 cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratch, cudaStream_t stream) {
   int sms = 0;
@@ -830,10 +909,12 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   }
   if (descs.empty()) return cudaSuccess;
   ProbDesc* dev = (ProbDesc*)scratch;
+  unsigned long long* counter = reinterpret_cast<unsigned long long*>(dev + std::max(count, 1));
   ExpandArgs* ea = new (std::nothrow) ExpandArgs;
   if (!ea) return cudaErrorMemoryAllocation;
   for (size_t off = 0; off < descs.size() && e == cudaSuccess; off += kDescPerExpand) {
     ea->out = dev + off;
+    ea->counter = off == 0 ? counter : nullptr;
     ea->count = (int)std::min<size_t>(kDescPerExpand, descs.size() - off);
     std::memcpy(ea->d, descs.data() + off, sizeof(ProbDesc) * ea->count);
     void* xargs[] = {ea};
@@ -844,10 +925,15 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   KArgs args;
   std::memset(&args, 0, sizeof(args));
   args.descs = dev;
+  args.chunk_counter = counter;
   args.nprob = (int)descs.size();
   args.sched = kSchedStreamK;
   args.total = total;
-  const int64_t grid = std::min<int64_t>(sms, total);
+  // Chunks of about 1/16 of a block's even share: blocks that meet cheaper iterations
+  // (fewer C targets per unit, TMA instead of cp.async staging) claim more of them.
+  args.chunk = std::max<int64_t>(1, (total + (int64_t)sms * kChunksPerBlock - 1) / ((int64_t)sms * kChunksPerBlock));
+  args.nchunks = (total + args.chunk - 1) / args.chunk;
+  const int64_t grid = std::min<int64_t>(sms, args.nchunks);
   void* kargs[] = {&args};
   return cudaLaunchKernel(pick_kernel(cls, true, tile), dim3((unsigned)grid), dim3(kThreads), kargs,
                           smem_bytes(cls, tile), stream);
