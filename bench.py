@@ -476,15 +476,15 @@ def main():
     launch_s = statistics.mean(per_launch)
     achieved = alg / launch_s / 1e9
     if args.dtype == "oz_bf16":
-        # tensor-core work of the slice products: 36 digit pairs x 2 h_m h_n h_k x 7^L
+        # tensor-core work of the slice products: 28 digit pairs x 2 h_m h_n h_k x 7^L
         P = 1 << L
 
         def padded(d, q):  # ceil(d / 2^L) rounded up to the tile edge q
             h = -(-d // P)
             return -(-h // q) * q
 
-        hmp, hnp, hkp = padded(m, 128), padded(n, 128), padded(k, 64)
-        mma = 36 * 2.0 * hmp * hnp * hkp * 7 ** L / launch_s / 1e12
+        hmp, hnp, hkp = padded(m, 128), padded(n, 256), padded(k, 64)
+        mma = 28 * 2.0 * hmp * hnp * hkp * 7 ** L / launch_s / 1e12
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
         bf16 = float(peaks.get("bf16_tflops", 1900.0))

@@ -11,13 +11,14 @@ ISC 2020).  The scheme computed here, step by step:
    max_k |X_ik| < 2^(e_i - 1)  (e_i = frexp(max)+1; rows of zeros get e_i = 0).
    For each column j of V: f_j likewise over max_k |V_kj|.  Then
    u_ik = X_ik * 2^-e_i and w_kj = V_kj * 2^-f_j lie in (-1/2, 1/2).
-2. Split into S balanced base-2^b digits (b = 7) in the integer domain:
+2. Split into S = 7 balanced base-2^b digits (b = 8) in the integer domain:
    N = rint(u * 2^(b S))  (u * 2^(bS) is an exact scaling; rint rounds half to even),
    so |N| <= 2^(bS-1).  Then, most significant first, with q_s = b (S - s):
    d_s = floor((N_s + 2^(q_s - 1)) / 2^(q_s)),  N_(s+1) = N_s - d_s 2^(q_s)
    for s < S, and d_S = N_S.  Hence N = sum_s d_s 2^(b (S - s)) exactly and
-   |d_s| <= 2^(b-1) = 64: every digit is exactly representable in BF16 and a product
-   of two digits is exact in FP32.  u = N 2^(-bS) + r with |r| <= 2^(-bS-1).
+   |d_s| <= 2^(b-1) = 128: every digit is exactly representable in BF16 (8 significant
+   bits) and a product of two digits (|.| <= 2^14) is exact in FP32.
+   u = N 2^(-bS) + r with |r| <= 2^(-bS-1).
 3. Products of slices.  For each weight w = 2 .. S+1, the exact integer matrix
    G_w = sum_{s + t = w} D_s^X D_t^V  (pairs with s + t > S + 1 are dropped).
 4. Recombine with one rounding: the integer T = sum_w G_w 2^(b(S+1-w)) is exact,
@@ -35,7 +36,8 @@ import numpy as np
 
 from . import tables
 
-B_BITS = 7
+B_BITS = 8      # bits per digit
+S_DIGITS = 7    # digits per operand: b S = 56 bits cover a 53-bit significand with rounding room
 
 
 def scale_exponents_rows(X: np.ndarray) -> np.ndarray:
@@ -83,7 +85,7 @@ def recombine(G: dict, e: np.ndarray, f: np.ndarray, S: int, b: int = B_BITS) ->
 
     T is carried as two integers, T_hi (weights w <= (S+2)//2) and T_lo (the rest),
     T = T_hi 2^(b(S+1-W)) + T_lo with W = (S+2)//2.  For the sizes this oracle serves
-    (|G_w| < 2^29) both are below 2^53 in magnitude, so each converts to FP64 exactly,
+    (|G_w| < 2^28) both are below 2^53 in magnitude (asserted), so each converts to FP64 exactly,
     the power-of-two scaling of T_hi is exact, and the one FP64 addition of the two
     returns the correctly rounded RN(T)."""
     W = (S + 2) // 2
@@ -99,7 +101,7 @@ def recombine(G: dict, e: np.ndarray, f: np.ndarray, S: int, b: int = B_BITS) ->
     return np.ldexp(T, (e[:, None] + f[None, :] - b * (S + 1)).astype(np.int64))
 
 
-def product(X: np.ndarray, V: np.ndarray, S: int = 8) -> np.ndarray:
+def product(X: np.ndarray, V: np.ndarray, S: int = S_DIGITS) -> np.ndarray:
     """M ~= X @ V by steps 1-4 (the split-precision product of one pair of operands)."""
     e = scale_exponents_rows(X)
     f = scale_exponents_rows(V.T)
@@ -110,7 +112,7 @@ def product(X: np.ndarray, V: np.ndarray, S: int = 8) -> np.ndarray:
     return recombine(slice_product_groups(DX, DV), e, f, S)
 
 
-def gemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int, S: int = 8) -> np.ndarray:
+def gemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int, S: int = S_DIGITS) -> np.ndarray:
     """C + A @ B with ``levels`` levels of Strassen (table of Eq. 4) and every product
     M_r computed by the split-precision product; returns a new array."""
     tab = tables.table(levels)

@@ -9,25 +9,29 @@
 //      smallest integer such that the row maximum is below 2^(e-1); round to the
 //      integer N = rint(x 2^(56 - e)) -- an exact scaling followed by round-to-nearest-
 //      even, done here with integer operations on the bits of x -- and cut N into
-//      S = 8 balanced base-128 digits (most significant first, d = floor((N + 2^(q-1))
-//      / 2^q)), |d| <= 64: exact in BF16;
-//   2. slice products (oz_gemm, tcgen05 + TMEM): for every weight w = s + t <= 9 the
-//      exact integer G_w = sum_{s+t=w} D_s^X D_t^V.  BF16 x BF16 products of digits are
-//      exact in FP32 and every FP32 accumulation chunk holds at most 1024 of them
-//      (|sum| < 2^22), so the tensor-core accumulator stays exact; the epilogue warps
-//      convert each chunk to an integer and fold the groups into two int64 Horner
-//      sums, T_hi = sum_{w<=5} G_w 2^(7(5-w)) and T_lo = sum_{w>=6} G_w 2^(7(9-w));
-//   3. recombine + scatter (oz_recombine_scatter): T = T_hi 2^28 + T_lo exactly in
-//      128-bit integers, M = RN(T) 2^(e_i + f_j - 63) with a single round-to-nearest-even
-//      conversion (integer operations), and C_q = C_q + gamma_q M_r for every product in
-//      table order (the ABC scatter, one owner thread per C element).
+//      S = 7 balanced base-256 digits (most significant first, d = floor((N + 2^(q-1))
+//      / 2^q)), |d| <= 128: exact in BF16 (8 significant bits);
+//   2. slice products (oz_gemm, tcgen05 + TMEM): for every weight w = s + t <= 8 (28
+//      digit pairs) the exact integer G_w = sum_{s+t=w} D_s^X D_t^V.  BF16 x BF16
+//      products of digits (|.| <= 2^14) are exact in FP32 and every FP32 accumulation
+//      chunk holds at most 256 of them (|sum| <= 2^22), so the tensor-core accumulator
+//      stays exact; the epilogue warps convert each chunk to int32 and sum the chunks of
+//      a weight (at most 16384 k per segment keeps the sum below 2^31);
+//   3. recombine + scatter (oz_recombine_scatter): T = sum_w G_w 2^(8(8-w)) exactly in
+//      128-bit integers (Horner over w, segments added), M = RN(T) 2^(e_i + f_j - 64)
+//      with a single round-to-nearest-even conversion (integer operations), and
+//      C_q = C_q + gamma_q M_r for every product in table order (the ABC scatter, one
+//      owner thread per C element).
 //
 // GB300 notes.  FP64 arithmetic runs at about 2 lanes per clock per SM here, so the
 // split and recombine steps use integer arithmetic for everything but the operand sums
 // and the final C additions; the products run on the BF16 tensor cores (tcgen05.mma
-// kind::f16, 128x128 tiles, accumulators in tensor memory) fed by TMA with 128-byte
-// swizzle.  INT8 slices are not used: the INT8 tensor rate of this part (measured
-// 150 TOP/s) is far below its BF16 rate (1950 TFLOP/s).
+// kind::f16, 128x256 tiles, accumulators in tensor memory) fed by TMA with 128-byte
+// swizzle.  The 128x256 tile moves 3/4 of the operand bytes per flop of a 128x128 one
+// (the 128x128 kernel was held by L2-to-SM bandwidth); int32 chunk sums keep its
+// 128 x 256 accumulator set in the epilogue warps' registers.  INT8 slices are not
+// used: the INT8 tensor rate of this part (measured 150 TOP/s) is far below its BF16
+// rate (1950 TFLOP/s).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -46,12 +50,13 @@ namespace {
 __constant__ PlanTables c_oz_plans = kPlanTables;
 __device__ int g_oz_status;
 
-constexpr int kS = 8;          // digits per operand
-constexpr int kB = 7;          // bits per digit
-constexpr int kWSplit = 5;     // groups 2..5 -> T_hi, 6..9 -> T_lo
-constexpr int kTM = 128, kTN = 128, kTK = 64;  // tile; kTK bf16 = one 128-byte row
-constexpr int kStages = 6;
-constexpr int kChunkItems = 16;  // k-blocks of 64 per exact FP32 chunk (1024 products)
+constexpr int kS = 7;          // digits per operand
+constexpr int kB = 8;          // bits per digit: |d| <= 128, exact in BF16
+constexpr int kGroups = kS;    // weights w = s + t = 2 .. kS + 1
+constexpr int kTM = 128, kTN = 256, kTK = 64;  // tile; kTK bf16 = one 128-byte row
+constexpr int kStages = 4;
+constexpr int kChunkItems = 4;   // k-blocks of 64 per exact FP32 chunk: 256 products, |sum| <= 2^22
+constexpr int kSegKB = 256;      // k-blocks per k segment: int32 group sums stay below 2^31
 constexpr int kThreads = 384;    // warp 0 TMA, warp 1 MMA + TMEM, warps 4..11 epilogue
 constexpr int kEpiThreads = 256;
 constexpr long long kWaitLimit = 2000000000LL;
@@ -345,25 +350,39 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
 // ---------------------------------------------------------------- slice-product kernel
 
 struct GemmArgs {
-  CUtensorMap tmA;  // DX of all products as rows [P*S*h_mp] x cols [h_kp], bf16
-  CUtensorMap tmB;  // DV of all products as rows [P*S*h_np] x cols [h_kp]
-  long long* t_hi;  // [P][h_mp][h_np]
-  long long* t_lo;
+  CUtensorMap tmA;  // DX of all products as rows [P*S*h_mp] x cols [h_kp], bf16, box 64 x 128
+  CUtensorMap tmB;  // DV of all products as rows [P*S*h_np] x cols [h_kp], bf16, box 64 x 256
+  int* G;           // [nseg][P][kGroups][h_mp][h_np] exact group sums G_w (w = 2 .. kS + 1) per k segment
   int P, tiles_m, tiles_n, nkb;
+  int nseg;         // k segments of kSegKB k-blocks (each segment's sums fit in int32)
   int64_t h_mp, h_np;
 };
 
-// Number of (pair, k-block) items of group w: pairs s + t = w with 1 <= s, t <= S.
+// Number of digit pairs (s, t) with s + t = w, 1 <= s, t <= S.
 __host__ __device__ constexpr int pairs_of(int w) {
   return (w - 1 < kS ? w - 1 : kS) - (w - kS > 1 ? w - kS : 1) + 1;
 }
 
+// Exact conversion of an FP32 integer value |v| <= 2^22 to int32: adding 1.5 * 2^23
+// puts v's integer bits in the low mantissa bits of a number in [2^23, 2^24].
+__device__ __forceinline__ int f32_int_exact(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+// Work unit u = (product p, tile t, k segment g): a 128 x 256 block of every G_w of
+// product p over the k-blocks of segment g (stored per segment; the recombination adds
+// the segments).  Warp 0 issues TMA loads of digit tiles
+// into a 4-stage ring, warp 1 issues tcgen05.mma (M = 128, N = 256, K = 16) into a
+// double-buffered FP32 accumulator in tensor memory (2 x 256 columns), and eight
+// epilogue warps turn every chunk of at most 256 digit products (|sum| <= 2^22, exact in
+// FP32) into int32 and sum the chunks of a weight w in registers; at the end of each
+// weight the exact G_w tile goes to global memory.
 __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ GemmArgs a) {
   extern __shared__ __align__(1024) uint8_t sm_raw[];
   // 1024-byte aligned stage ring for the 128-byte swizzle
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* stA = sm;                               // [kStages][128][128 B]
-  uint8_t* stB = sm + kStages * kTM * 128;         // [kStages][128][128 B]
+  uint8_t* stA = sm;                               // [kStages][128 rows][128 B]
+  uint8_t* stB = sm + kStages * kTM * 128;         // [kStages][256 rows][128 B]
   uint64_t* bars = reinterpret_cast<uint64_t*>(stB + kStages * kTN * 128);
   uint64_t* full = bars;
   uint64_t* empty = bars + kStages;
@@ -381,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(smem_u32(tmem_slot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     tc_fence_before();
@@ -391,10 +410,17 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
   const uint32_t tmem = *tmem_slot;
 
   const int tiles = a.tiles_m * a.tiles_n;
-  const int units = a.P * tiles;
-  int group_items[kS + 2];
-#pragma unroll
-  for (int w = 2; w <= kS + 1; ++w) group_items[w] = pairs_of(w) * a.nkb;
+  const int units = a.P * tiles * a.nseg;
+  auto unit_of = [&](int u, int* p, int* tm, int* tn, int* kb0, int* kb1) {
+    const int per_p = tiles * a.nseg;
+    *p = u / per_p;
+    const int rem = u - *p * per_p;
+    const int t = rem / a.nseg, g = rem - (rem / a.nseg) * a.nseg;
+    *tm = t / a.tiles_n;
+    *tn = t - (t / a.tiles_n) * a.tiles_n;
+    *kb0 = g * kSegKB;
+    *kb1 = (g + 1) * kSegKB < a.nkb ? (g + 1) * kSegKB : a.nkb;
+  };
 
   if (warp < 4) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kLowRegs));
@@ -403,15 +429,15 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
       uint32_t it = 0;
       bool bad = false;
       for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
-        const int p = u / tiles, t = u - (u / tiles) * tiles;
-        const int tm = t / a.tiles_n, tn = t - (t / a.tiles_n) * a.tiles_n;
+        int p, tm, tn, kb0, kb1;
+        unit_of(u, &p, &tm, &tn, &kb0, &kb1);
         for (int w = 2; w <= kS + 1 && !bad; ++w) {
           const int s_lo = w - kS > 1 ? w - kS : 1, s_hi = w - 1 < kS ? w - 1 : kS;
           for (int s = s_lo; s <= s_hi && !bad; ++s) {
             const int tt = w - s;
             const int ya = (int)(((int64_t)p * kS + (s - 1)) * a.h_mp + (int64_t)tm * kTM);
             const int yb = (int)(((int64_t)p * kS + (tt - 1)) * a.h_np + (int64_t)tn * kTN);
-            for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = it % kStages;
               const uint32_t use = it / kStages;
               if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) { bad = true; break; }
@@ -432,8 +458,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
       uint32_t it = 0, ch = 0;
       bool bad = false;
       for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+        int p, tm, tn, kb0, kb1;
+        unit_of(u, &p, &tm, &tn, &kb0, &kb1);
         for (int w = 2; w <= kS + 1 && !bad; ++w) {
-          const int n_items = group_items[w];
+          const int n_items = pairs_of(w) * (kb1 - kb0);
           for (int c0 = 0; c0 < n_items && !bad; c0 += kChunkItems, ++ch) {
             const int buf = ch & 1;
             const uint32_t use = ch >> 1;
@@ -467,48 +495,41 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
     // ------------------------------------------------ epilogue warps
     const int ew = warp - 4;
     const int g = warp & 3;         // TMEM lane quarter this warp may read
-    const int half = ew >> 2;       // column half of the tile
+    const int half = ew >> 2;       // column half (128 columns) of the tile
     uint32_t ch = 0;
     bool bad = false;
-    long long R[64];
+    int R[128];
     for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
-      const int p = u / tiles, t = u - (u / tiles) * tiles;
-      const int tm = t / a.tiles_n, tn = t - (t / a.tiles_n) * a.tiles_n;
-#pragma unroll
-      for (int q = 0; q < 64; ++q) R[q] = 0;
+      int p, tm, tn, kb0, kb1;
+      unit_of(u, &p, &tm, &tn, &kb0, &kb1);
       const int64_t row = (int64_t)tm * kTM + 32 * g + lane;
-      const int64_t col0 = (int64_t)tn * kTN + 64 * half;
+      const int64_t col0 = (int64_t)tn * kTN + 128 * half;
       for (int w = 2; w <= kS + 1 && !bad; ++w) {
-        if (w != 2 && w != kWSplit + 1) {
 #pragma unroll
-          for (int q = 0; q < 64; ++q) R[q] *= (1LL << kB);
-        }
-        const int n_items = group_items[w];
+        for (int q = 0; q < 128; ++q) R[q] = 0;
+        const int n_items = pairs_of(w) * (kb1 - kb0);
         for (int c0 = 0; c0 < n_items; c0 += kChunkItems, ++ch) {
           const int buf = ch & 1;
           if (!mbar_wait(&tfull[buf], (ch >> 1) & 1)) { bad = true; break; }
           tc_fence_after();
-          const uint32_t base = tmem + ((uint32_t)(32 * g) << 16) + buf * kTN + 64 * half;
+          const uint32_t base = tmem + ((uint32_t)(32 * g) << 16) + buf * kTN + 128 * half;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 8; ++q) {
             uint32_t v[16];
             tmem_ld16(base + 16 * q, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 16; ++i) R[16 * q + i] += (long long)__float2int_rn(__uint_as_float(v[i]));
+            for (int i = 0; i < 16; ++i) R[16 * q + i] += f32_int_exact(v[i]);
           }
           tc_fence_before();
           mbar_arrive(&tempty[buf]);
         }
         if (bad) break;
-        if (w == kWSplit || w == kS + 1) {
-          long long* dst = (w == kWSplit ? a.t_hi : a.t_lo) + ((int64_t)p * a.h_mp + row) * a.h_np + col0;
-          longlong2* d2 = reinterpret_cast<longlong2*>(dst);
+        const int seg = kb0 / kSegKB;
+        int* dst = a.G + ((((int64_t)seg * a.P + p) * kGroups + (w - 2)) * a.h_mp + row) * a.h_np + col0;
+        int4* d4 = reinterpret_cast<int4*>(dst);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) d2[q] = make_longlong2(R[2 * q], R[2 * q + 1]);
-#pragma unroll
-          for (int q = 0; q < 64; ++q) R[q] = 0;
-        }
+        for (int q = 0; q < 32; ++q) d4[q] = make_int4(R[4 * q], R[4 * q + 1], R[4 * q + 2], R[4 * q + 3]);
       }
     }
     if (bad) {
@@ -518,7 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
   }
 }
 
@@ -530,21 +551,15 @@ struct RecombineArgs {
   int64_t hm, hn, h_mp, h_np;
   int levels, P;
   int plan_off;   // table row of product 0 of the level
-  const long long* t_hi;
-  const long long* t_lo;
+  const int* G;   // [nseg][P][kGroups][h_mp][h_np]
+  int nseg;
   const int* e;   // [P][h_mp]
   const int* f;   // [P][h_np]
 };
 
-// RN(T) * 2^scale for T = hi * 2^28 + lo, with integer operations (one rounding).
-__device__ double round_scaled(long long hi, long long lo, int scale) {
-  // 128-bit two's complement T = (th, tl)
-  unsigned long long tl = (unsigned long long)hi << 28;
-  long long th = hi >> 36;
-  const unsigned long long l2 = (unsigned long long)lo;
-  const unsigned long long sum = tl + l2;
-  th += (lo >> 63) + (sum < tl ? 1 : 0);
-  tl = sum;
+// RN(T) * 2^scale for the 128-bit two's complement integer T = th * 2^64 + tl, with
+// integer operations (one rounding).
+__device__ double round_i128(long long th, unsigned long long tl, int scale) {
   if (th == 0 && tl == 0) return 0.0;
   const bool neg = th < 0;
   unsigned long long mh = (unsigned long long)th, ml = tl;
@@ -615,9 +630,23 @@ __global__ void oz_recombine_scatter(const __grid_constant__ RecombineArgs a) {
       for (int t = 0; t < nc; ++t) {
         const uint8_t code = c_oz_plans.tc[row][t];
         if (term_bi(code) != qi || term_bj(code) != qj) continue;
-        const int64_t o = ((int64_t)r * a.h_mp + i) * a.h_np + j;
-        const double M = round_scaled(a.t_hi[o], a.t_lo[o],
-                                      a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
+        // T = sum_w G_w 2^(b (S + 1 - w)), by Horner over w in 128-bit integers.
+        long long th = 0;
+        unsigned long long tl = 0;
+        const int64_t plane = a.h_mp * a.h_np;
+        const int* g = a.G + (int64_t)r * kGroups * plane + i * a.h_np + j;
+#pragma unroll
+        for (int w = 0; w < kGroups; ++w) {
+          th = (long long)(((unsigned long long)th << kB) | (tl >> (64 - kB)));
+          tl <<= kB;
+          long long gw = 0;
+          for (int sg = 0; sg < a.nseg; ++sg) gw += g[((int64_t)sg * a.P * kGroups + w) * plane];
+          const unsigned long long nl = tl + (unsigned long long)gw;
+          th += (gw >> 63) + (nl < tl ? 1 : 0);
+          tl = nl;
+        }
+        const double M = round_i128(th, tl,
+                                    a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
         c = term_neg(code) ? c - M : c + M;
       }
     }
@@ -649,10 +678,10 @@ void oz_init() {
                                      (int)kSplitColsSmem);
 }
 
-bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols) {
+bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows) {
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(cols * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM};
+  cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return g_oz_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -667,7 +696,9 @@ int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
   const int64_t P = kPlanCount[levels];
   const int64_t hmp = round_up(block_edge(m, levels), kTM), hnp = round_up(block_edge(n, levels), kTN),
                 hkp = round_up(block_edge(k, levels), kTK);
-  return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + 2 * P * hmp * hnp * 8 + P * hnp * 8 + 4096;
+  const int64_t nseg = (hkp / kTK + kSegKB - 1) / kSegKB;
+  return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + nseg * kGroups * P * hmp * hnp * 4 + P * hnp * 8 +
+         4096;
 }
 
 int ozaki_device_status() {
@@ -695,8 +726,8 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   int* ex = (int*)w;                                           w += (size_t)P * hmp * 4;
   int* fx = (int*)w;                                           w += (size_t)P * hnp * 4;
   w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
-  long long* thi = (long long*)w;                              w += (size_t)P * hmp * hnp * 8;
-  long long* tlo = (long long*)w;                              w += (size_t)P * hmp * hnp * 8;
+  const int nseg = (int)((hkp / kTK + kSegKB - 1) / kSegKB);
+  int* G = (int*)w;                                            w += (size_t)nseg * kGroups * P * hmp * hnp * 4;
   unsigned long long* colmax = (unsigned long long*)w;  // [P][h_np] magnitude bits
 
   SplitArgs sa;
@@ -730,14 +761,16 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
 
   GemmArgs ga;
   std::memset(&ga, 0, sizeof(ga));
-  if (!encode_bf16(&ga.tmA, DX, (int64_t)P * kS * hmp, hkp) || !encode_bf16(&ga.tmB, DV, (int64_t)P * kS * hnp, hkp))
+  if (!encode_bf16(&ga.tmA, DX, (int64_t)P * kS * hmp, hkp, kTM) ||
+      !encode_bf16(&ga.tmB, DV, (int64_t)P * kS * hnp, hkp, kTN))
     return cudaErrorInvalidValue;
-  ga.t_hi = thi; ga.t_lo = tlo;
+  ga.G = G;
   ga.P = P;
   ga.tiles_m = (int)(hmp / kTM); ga.tiles_n = (int)(hnp / kTN);
   ga.nkb = (int)(hkp / kTK);
+  ga.nseg = nseg;
   ga.h_mp = hmp; ga.h_np = hnp;
-  const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n;
+  const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n * ga.nseg;
   const int grid = (int)std::min<int64_t>(sms, units);
   void* gargs[] = {&ga};
   e = cudaLaunchKernel((const void*)oz_gemm, dim3(grid), dim3(kThreads), gargs, oz_gemm_smem(), stream);
@@ -747,7 +780,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   ra.C = C; ra.ldc = ldc; ra.m = m; ra.n = n;
   ra.hm = hm; ra.hn = hn; ra.h_mp = hmp; ra.h_np = hnp;
   ra.levels = levels; ra.P = P; ra.plan_off = kPlanOffset[levels];
-  ra.t_hi = thi; ra.t_lo = tlo; ra.e = ex; ra.f = fx;
+  ra.G = G; ra.nseg = nseg; ra.e = ex; ra.f = fx;
   const int64_t total = hm * hn * (1LL << (2 * levels));
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)sms * 32);

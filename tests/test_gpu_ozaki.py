@@ -97,3 +97,21 @@ def test_int8_slices_not_built():
     st = sg.strassen_gemm(4, 4, 4, A.data_ptr(), 4, A.data_ptr(), 4, C.data_ptr(), 4, 0, 0,
                           sg.STRASSEN_F64_OZ_INT8, 0)
     assert st == -5
+
+
+def test_extreme_digits_fill_the_exact_chunk_bound():
+    """Every entry 0.5 - 2^-54 (top digit 128): each 256-product FP32 chunk of the
+    top-digit pair sums to exactly 2^22, the largest value the exactness argument
+    allows; the result must still match the scheme bit for bit."""
+    x = 0.5 - 2.0 ** -54
+    A, B = np.full((64, 512), x), np.full((512, 64), -x)
+    C = np.zeros((64, 64))
+    ref = ozaki.gemm(A, B, C, 0)
+    assert np.array_equal(run(A, B, C, 0), ref)
+
+
+def test_long_reduction_uses_several_k_segments():
+    """k = 16448 needs two k segments (each keeps the int32 group sums below 2^31);
+    the recombination adds them exactly."""
+    A, B, C = W.uniform(70, 16448, 21), W.uniform(16448, 50, 22), W.uniform(70, 50, 23)
+    assert np.array_equal(run(A, B, C, 0), ozaki.gemm(A, B, C, 0))
