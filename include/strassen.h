@@ -138,6 +138,34 @@ STRASSEN_API int classical_gemm(int64_t m, int64_t n, int64_t k,
                    double* C, int64_t ldc,
                    strassen_stream_t stream);
 
+/*
+ * strassen_dgemm -- the full BLAS operation C = alpha op(A) op(B) + beta C with the
+ * Strassen family, so the library can stand in for a DGEMM call (the paper's reduction
+ * of DGEMM to C = alpha A B + C in Section 2.2 and its plug-compatibility aim of
+ * Section 1; row-major here, as everywhere in this library).
+ *
+ *   transa, transb   0: op(X) = X; 1: op(X) = X^T.  op(A) is m x k, op(B) is k x n.
+ *   A, lda           stored m x k (lda >= k) when transa = 0, k x m (lda >= m) when 1.
+ *   B, ldb           stored k x n (ldb >= n) when transb = 0, n x k (ldb >= k) when 1.
+ *   alpha, beta      scalars.  beta = 0 sets C to alpha op(A) op(B) without reading C
+ *                    (NaNs in C do not propagate); alpha = 0 or k = 0 only scales C.
+ *   C, ldc           m x n, ldc >= n; must not overlap A or B.
+ *   levels, variant, dtype, stream   as strassen_gemm (levels -1 / STRASSEN_AUTO choose).
+ *
+ * Order of operations: C = beta C (one multiply per element, skipped for beta = 1),
+ * then the product is added as in strassen_gemm with every partial product M_r scaled
+ * by alpha where it is added into C (the epilogue of ABC, the C updates of AB and
+ * Naive, the recombination of the split-precision path): for alpha = beta = 1 and no
+ * transposes the result is that of strassen_gemm.  Transposed operands are read in
+ * place (no copies): the FP64 kernel loads their tiles with the other box orientation.
+ * Returns STRASSEN_OK or a negative status (STRASSEN_ERR_ARG for transa or transb
+ * outside {0, 1}).
+ */
+STRASSEN_API int strassen_dgemm(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                                double* C, int64_t ldc, int levels, strassen_variant variant,
+                                strassen_dtype dtype, strassen_stream_t stream);
+
 /* One problem of a batched call: C += A*B as in strassen_gemm. */
 typedef struct {
   int64_t m, n, k;

@@ -9,6 +9,7 @@ Contents
 * :func:`gemm`, :func:`strassen`, :func:`gemm_sampled` -- thin numpy wrappers over
   the plain C in ``oracle.c`` (classical definition, Section 2.1; recursive textbook
   Strassen per Figure 1, Sections 3.1-3.3; Dot2-compensated sampled entries).
+* :func:`dgemm` -- alpha op(A) op(B) + beta C by that definition (Section 2.2).
 * :mod:`oracle.tables` -- the one-level table of Figure 1 and the L-level tables of
   Eq. 4 built as Kronecker powers of it (Sections 3.5-3.6).
 * :mod:`oracle.ozaki` -- error-free splitting of FP64 operands into integer slices
@@ -87,6 +88,21 @@ def gemm(A: np.ndarray, B: np.ndarray, C: np.ndarray) -> int:
     if r < 0:
         raise MemoryError("oracle_gemm")
     return int(r)
+
+
+def dgemm(transa: int, transb: int, alpha: float, A: np.ndarray, B: np.ndarray, beta: float,
+          C: np.ndarray) -> np.ndarray:
+    """The BLAS operation alpha op(A) op(B) + beta C (Section 2.2's DGEMM before its
+    reduction to alpha = beta = 1), op(X) = X^T when trans is set: the product by the
+    classical definition (:func:`gemm` on op(A), op(B)), then one scaling of it and of C
+    and one addition per entry.  beta = 0 does not read C.  Returns a new array."""
+    Aop = np.ascontiguousarray(A.T if transa else A, dtype=np.float64)
+    Bop = np.ascontiguousarray(B.T if transb else B, dtype=np.float64)
+    P = np.zeros((Aop.shape[0], Bop.shape[1]))
+    if Aop.shape[1] > 0:
+        gemm(Aop, Bop, P)
+    base = np.zeros_like(P) if beta == 0 else beta * np.asarray(C, dtype=np.float64)
+    return base + alpha * P
 
 
 def strassen(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int) -> int:

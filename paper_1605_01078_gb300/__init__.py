@@ -17,6 +17,7 @@ from . import _binding
 from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  # noqa: F401
                        STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_NAIVE, StrassenError,
                        classical_gemm, strassen_gemm, strassen_gemm_ab_noalloc, strassen_gemm_batched,
+                       strassen_dgemm,
                        strassen_plan_table,
                        strassen_problem, strassen_select, strassen_status_string, strassen_device_status,
                        strassen_check_wait_timeout, strassen_tune_record, strassen_tune_clear,
@@ -63,6 +64,23 @@ def gemm(A, B, C, levels: int = 1, variant="ABC", dtype="f64", stream=None) -> N
     st = strassen_gemm(m, n, k, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
                        int(levels), v, d, _stream(stream))
     _binding._check(st, "strassen_gemm")
+
+
+def dgemm(A, B, C, alpha: float = 1.0, beta: float = 1.0, trans_a: bool = False, trans_b: bool = False,
+          levels: int = 1, variant="ABC", dtype="f64", stream=None) -> None:
+    """In place on the stream: C = alpha op(A) op(B) + beta C, op(X) = X.T when trans_x.
+    A and B are the stored matrices (A is k x m when trans_a); transposes are read in
+    place by the kernels."""
+    A, B, C = _mat(A, "A"), _mat(B, "B"), _mat(C, "C")
+    m, k = (A.shape[1], A.shape[0]) if trans_a else (A.shape[0], A.shape[1])
+    k2, n = (B.shape[1], B.shape[0]) if trans_b else (B.shape[0], B.shape[1])
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError(f"shape mismatch: op(A) {m}x{k}, op(B) {k2}x{n}, C {tuple(C.shape)}")
+    v = VARIANTS[variant.upper()] if isinstance(variant, str) else int(variant)
+    d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    st = strassen_dgemm(int(bool(trans_a)), int(bool(trans_b)), m, n, k, float(alpha), A.data_ptr(), _ld(A),
+                        B.data_ptr(), _ld(B), float(beta), C.data_ptr(), _ld(C), int(levels), v, d, _stream(stream))
+    _binding._check(st, "strassen_dgemm")
 
 
 def classical(A, B, C, stream=None) -> None:

@@ -52,6 +52,8 @@ SIGNATURES = {
     "strassen_workspace_size": (_I64, [_I64, _I64, _I64, _I, _I, _I]),
     "strassen_status_string": (ctypes.c_char_p, [_I]),
     "strassen_plan_table": (_I, [_I, _I, _IP, _IP, _IP, _IP, _IP, _IP]),
+    "strassen_dgemm": (_I, [_I, _I, _I64, _I64, _I64, ctypes.c_double, _P, _I64, _P, _I64, ctypes.c_double,
+                            _P, _I64, _I, _I, _I, _P]),
     "strassen_gemm_ab_noalloc": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _P]),
     "strassen_device_status": (_I, [_P]),
     "strassen_tune_record": (_I, [_I64, _I64, _I64, _I, _I, _I, _I]),
@@ -101,6 +103,13 @@ def strassen_gemm(m, n, k, A, lda, B, ldb, C, ldc, levels, variant, dtype, strea
 
 def classical_gemm(m, n, k, A, lda, B, ldb, C, ldc, stream) -> int:
     return lib().classical_gemm(m, n, k, A, lda, B, ldb, C, ldc, stream)
+
+
+def strassen_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, dtype,
+                   stream) -> int:
+    """C = alpha op(A) op(B) + beta C (row-major BLAS semantics); returns the status."""
+    return lib().strassen_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant,
+                                dtype, stream)
 
 
 def strassen_gemm_ab_noalloc(m, n, k, A, lda, B, ldb, C, ldc, levels, stream) -> int:

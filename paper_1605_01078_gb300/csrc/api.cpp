@@ -39,6 +39,34 @@ int check_args(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, co
   return 0;
 }
 
+// BLAS options of strassen_dgemm: op(A), op(B) and the scale of the product.
+struct Op {
+  int ta = 0, tb = 0;
+  double alpha = 1.0;
+};
+
+// Argument checks of strassen_dgemm (stored shapes follow the transposes).  Returns 1
+// when there is no product to compute, 0 when it should proceed, or a negative status.
+int check_args_op(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                  int64_t ldb, const double* C, int64_t ldc, const Op& op) {
+  if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
+  if (m == 0 || n == 0) return 1;
+  if (!C) return STRASSEN_ERR_NULL;
+  if (ldc < n) return STRASSEN_ERR_LD;
+  if (k == 0 || op.alpha == 0.0) return 1;
+  if (!A || !B) return STRASSEN_ERR_NULL;
+  const int64_t ar = op.ta ? k : m, ac = op.ta ? m : k, br = op.tb ? n : k, bc = op.tb ? k : n;
+  if (lda < ac || ldb < bc) return STRASSEN_ERR_LD;
+  const char* a0 = (const char*)A;
+  const char* a1 = (const char*)(A + (ar - 1) * lda + ac);
+  const char* b0 = (const char*)B;
+  const char* b1 = (const char*)(B + (br - 1) * ldb + bc);
+  const char* c0 = (const char*)C;
+  const char* c1 = (const char*)(C + (m - 1) * ldc + n);
+  if ((c0 < a1 && a0 < c1) || (c0 < b1 && b0 < c1)) return STRASSEN_ERR_ARG;
+  return 0;
+}
+
 int clamp_levels(int levels, int64_t m, int64_t n, int64_t k) {
   int64_t mn = m < n ? m : n;
   mn = mn < k ? mn : k;
@@ -49,10 +77,12 @@ int clamp_levels(int levels, int64_t m, int64_t n, int64_t k) {
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? STRASSEN_OK : STRASSEN_ERR_CUDA; }
 
 int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                  int64_t ldb, double* C, int64_t ldc, EpilogueKind owner_epi, cudaStream_t s, int tile = -1) {
+                  int64_t ldb, double* C, int64_t ldc, EpilogueKind owner_epi, cudaStream_t s, int tile = -1,
+                  const Op& op = Op()) {
   Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, C, ldc, 0);
   L.epi = owner_epi;
   L.tile = tile;
+  L.trans_a = op.ta; L.trans_b = op.tb; L.alpha = op.alpha;
   choose_fp64_schedule(&L, deterministic_requested());
   if (owner_epi == kEpiStore) {
     // The kernel accumulates into its target: a store is a clear followed by the adds.
@@ -63,10 +93,11 @@ int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
 }
 
 int run_abc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-            int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile) {
+            int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile, const Op& op = Op()) {
   Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, C, ldc, levels);
   L.epi = kEpiAtomicAdd;
   L.tile = tile;
+  L.trans_a = op.ta; L.trans_b = op.tb; L.alpha = op.alpha;
   choose_fp64_schedule(&L, deterministic_requested());
   return cuda_status(launch_fp64(L, s));
 }
@@ -80,7 +111,7 @@ struct Workspace {
 };
 
 int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-           int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile) {
+           int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile, const Op& op = Op()) {
   Plan pl;
   if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels);
@@ -100,20 +131,21 @@ int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
     L.m_target = 1;
     L.epi = kEpiStore;
     L.tile = tile;
+    L.trans_a = op.ta; L.trans_b = op.tb;  // alpha is applied by the C updates
     choose_fp64_schedule(&L, deterministic_requested());
     // The kernel accumulates into M: clear it first.
     if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
     cudaError_t e = launch_fp64(L, s);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
-    // ... then the separate updates C_q += gamma_q M_r.
-    e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s);
+    // ... then the separate updates C_q += gamma_q alpha M_r.
+    e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s, op.alpha);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
   }
   return STRASSEN_OK;
 }
 
 int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-              int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile) {
+              int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile, const Op& op = Op()) {
   Plan pl;
   if (!make_plan(levels, &pl)) return STRASSEN_ERR_LEVELS;
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
@@ -129,20 +161,20 @@ int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, con
   double* V = X + hm * hk;
   double* M = V + hk * hn;
   for (int r = 0; r < pl.nprod; ++r) {
-    cudaError_t e = launch_block_sum(X, hm, hk, A, lda, m, k, hm, hk, pl.ta[r], pl.na[r], s);
+    cudaError_t e = launch_block_sum(X, hm, hk, A, lda, m, k, hm, hk, pl.ta[r], pl.na[r], s, op.ta);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
-    e = launch_block_sum(V, hk, hn, B, ldb, k, n, hk, hn, pl.tb[r], pl.nb[r], s);
+    e = launch_block_sum(V, hk, hn, B, ldb, k, n, hk, hn, pl.tb[r], pl.nb[r], s, op.tb);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
     int st = run_classical(hm, hn, hk, X, hk, V, hn, M, hn, kEpiStore, s, tile);
     if (st != STRASSEN_OK) return st;
-    e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s);
+    e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s, op.alpha);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
   }
   return STRASSEN_OK;
 }
 
 int run_oz(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-           double* C, int64_t ldc, int levels, cudaStream_t s) {
+           double* C, int64_t ldc, int levels, cudaStream_t s, const Op& op = Op()) {
   Workspace ws;
   ws.s = s;
   if (cudaMallocAsync(&ws.p, (size_t)ozaki_workspace_bytes(m, n, k, levels), s) != cudaSuccess) {
@@ -150,7 +182,40 @@ int run_oz(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
     ws.p = nullptr;
     return STRASSEN_ERR_ALLOC;
   }
-  return cuda_status(run_ozaki(m, n, k, A, lda, B, ldb, C, ldc, levels, ws.p, s));
+  return cuda_status(run_ozaki(m, n, k, A, lda, B, ldb, C, ldc, levels, ws.p, s, op.ta, op.tb, op.alpha));
+}
+
+// The product C += alpha op(A) op(B) with the requested (or selected) plan; arguments
+// already checked.
+int run_product(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                double* C, int64_t ldc, int levels, strassen_variant variant, strassen_dtype dtype, cudaStream_t s,
+                const Op& op) {
+  if (dtype == STRASSEN_F64_OZ_INT8) return STRASSEN_ERR_UNSUPPORTED;
+  int tile = -1;  // the launch's own choice unless the selector picked the whole plan
+  if (levels == -1 || variant == STRASSEN_AUTO) {
+    int sl = 0, st_tile = 0;
+    strassen_variant sv = STRASSEN_ABC;
+    const int st = strassen_select(m, n, k, dtype, &sl, &sv, &st_tile);
+    if (st != STRASSEN_OK) return st;
+    if (levels == -1 && variant == STRASSEN_AUTO) tile = st_tile;
+    if (levels == -1) levels = sl;
+    if (variant == STRASSEN_AUTO) variant = sv;
+  }
+  const int requested_levels = levels;
+  levels = clamp_levels(levels, m, n, k);
+  if (levels != requested_levels) tile = -1;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return STRASSEN_ERR_CUDA;
+  }
+  if (dtype == STRASSEN_F64_OZ_BF16) return run_oz(m, n, k, A, lda, B, ldb, C, ldc, levels, s, op);
+  if (levels == 0) return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, s, tile, op);
+  switch (variant) {
+    case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
+    case STRASSEN_AB: return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
+    case STRASSEN_NAIVE: return run_naive(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
+    default: return STRASSEN_ERR_UNSUPPORTED;
+  }
 }
 
 }  // namespace
@@ -167,33 +232,31 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
     const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
     if (chk < 0) return chk;
     if (chk == 1) return STRASSEN_OK;
+    return run_product(m, n, k, A, lda, B, ldb, C, ldc, levels, variant, dtype, (cudaStream_t)stream, Op());
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
+}
+
+int strassen_dgemm(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int levels,
+                   strassen_variant variant, strassen_dtype dtype, strassen_stream_t stream) {
+  try {
+    if (transa < 0 || transa > 1 || transb < 0 || transb > 1) return STRASSEN_ERR_ARG;
+    if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
+    if ((int)variant < 0 || (int)variant > 3) return STRASSEN_ERR_UNSUPPORTED;
+    if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
+    Op op;
+    op.ta = transa; op.tb = transb; op.alpha = alpha;
+    const int chk = check_args_op(m, n, k, A, lda, B, ldb, C, ldc, op);
+    if (chk < 0) return chk;
+    if (m == 0 || n == 0) return STRASSEN_OK;
     if (dtype == STRASSEN_F64_OZ_INT8) return STRASSEN_ERR_UNSUPPORTED;
-    int tile = -1;  // the launch's own choice unless the selector picked the whole plan
-    if (levels == -1 || variant == STRASSEN_AUTO) {
-      int sl = 0, st_tile = 0;
-      strassen_variant sv = STRASSEN_ABC;
-      const int st = strassen_select(m, n, k, dtype, &sl, &sv, &st_tile);
-      if (st != STRASSEN_OK) return st;
-      if (levels == -1 && variant == STRASSEN_AUTO) tile = st_tile;
-      if (levels == -1) levels = sl;
-      if (variant == STRASSEN_AUTO) variant = sv;
-    }
-    const int requested_levels = levels;
-    levels = clamp_levels(levels, m, n, k);
-    if (levels != requested_levels) tile = -1;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaPeekAtLastError() != cudaSuccess) {
-      cudaGetLastError();
-      return STRASSEN_ERR_CUDA;
-    }
-    if (dtype == STRASSEN_F64_OZ_BF16) return run_oz(m, n, k, A, lda, B, ldb, C, ldc, levels, s);
-    if (levels == 0) return run_classical(m, n, k, A, lda, B, ldb, C, ldc, kEpiRmw, s, tile);
-    switch (variant) {
-      case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile);
-      case STRASSEN_AB: return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile);
-      case STRASSEN_NAIVE: return run_naive(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile);
-      default: return STRASSEN_ERR_UNSUPPORTED;
-    }
+    // C = beta C first (BLAS: beta = 0 ignores what C held), then C += alpha op(A) op(B).
+    if (launch_scale(C, ldc, m, n, beta, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
+    if (chk == 1) return STRASSEN_OK;
+    return run_product(m, n, k, A, lda, B, ldb, C, ldc, levels, variant, dtype, s, op);
   } catch (...) {
     return STRASSEN_ERR_ALLOC;
   }

@@ -98,6 +98,8 @@ struct alignas(128) ProbDesc {
   int32_t epi;
   int32_t tiles_m, tiles_n, ksteps;
   int32_t use_tma;
+  int32_t trans_a, trans_b;  // op(A) = A^T (A stored k x m), op(B) = B^T (B stored n x k)
+  double alpha;              // the product is scaled by alpha in the scatter
 };
 
 struct KArgs {
@@ -369,13 +371,17 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
           mbar_arrive_expect_tx(&raw_full[slot], (uint32_t)((na * BM * BK + nb * BK * BN) * sizeof(double)));
           for (int t = 0; t < na; ++t) {
             const uint8_t code = c_plans.ta[row][t];
-            tma_load_2d(ra + t * BM * BK, &d.tmA, (int)(term_bj(code) * d.hk + (int64_t)c.ks * BK),
-                        (int)(term_bi(code) * d.hm + (int64_t)tm * BM), &raw_full[slot]);
+            const int rr = (int)(term_bi(code) * d.hm + (int64_t)tm * BM), kc = (int)(term_bj(code) * d.hk + (int64_t)c.ks * BK);
+            // A box [BM][BK] (row, k), or for A^T the stored box [BK][BM] (k, row)
+            if (d.trans_a) tma_load_2d(ra + t * BM * BK, &d.tmA, rr, kc, &raw_full[slot]);
+            else tma_load_2d(ra + t * BM * BK, &d.tmA, kc, rr, &raw_full[slot]);
           }
           for (int t = 0; t < nb; ++t) {
             const uint8_t code = c_plans.tb[row][t];
-            tma_load_2d(rb + t * BK * BN, &d.tmB, (int)(term_bj(code) * d.hn + (int64_t)tn * BN),
-                        (int)(term_bi(code) * d.hk + (int64_t)c.ks * BK), &raw_full[slot]);
+            const int kr = (int)(term_bi(code) * d.hk + (int64_t)c.ks * BK), cc = (int)(term_bj(code) * d.hn + (int64_t)tn * BN);
+            // B box [BK][BN] (k, col), or for B^T the stored box [BN][BK] (col, k)
+            if (d.trans_b) tma_load_2d(rb + t * BK * BN, &d.tmB, kr, cc, &raw_full[slot]);
+            else tma_load_2d(rb + t * BK * BN, &d.tmB, cc, kr, &raw_full[slot]);
           }
         } else {
           mbar_arrive(&raw_full[slot]);
@@ -387,11 +393,13 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
           for (int q = 0; q < (BM * BK) / kProducers; ++q) {
             const int e = pt + q * kProducers;
-            const int i = e / BK, kk = e - (e / BK) * BK;
+            // raw layout [BM][BK], or [BK][BM] for A^T (the layout of the TMA box)
+            const int i = d.trans_a ? e % BM : e / BK, kk = d.trans_a ? e / BM : e % BK;
             const int64_t li = (int64_t)tm * BM + i, lk = (int64_t)c.ks * BK + kk;
-            const int64_t gr = r0 + li, gc = c0 + lk;
+            const int64_t gr = r0 + li, gc = c0 + lk;  // element (gr, gc) of op(A)
             const bool ok = li < d.hm && lk < d.hk && gr < d.a_rows && gc < d.a_cols;
-            cp_async8(ra + t * BM * BK + e, ok ? d.A + gr * d.lda + gc : d.A, ok ? 8 : 0);
+            const double* src = d.trans_a ? d.A + gc * d.lda + gr : d.A + gr * d.lda + gc;
+            cp_async8(ra + t * BM * BK + e, ok ? src : d.A, ok ? 8 : 0);
           }
         }
         for (int t = 0; t < nb; ++t) {
@@ -400,11 +408,13 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
           for (int q = 0; q < (BN * BK) / kProducers; ++q) {
             const int e = pt + q * kProducers;
-            const int kk = e / BN, jj = e - (e / BN) * BN;
+            // raw layout [BK][BN], or [BN][BK] for B^T
+            const int kk = d.trans_b ? e % BK : e / BN, jj = d.trans_b ? e / BK : e % BN;
             const int64_t lk = (int64_t)c.ks * BK + kk, lj = (int64_t)tn * BN + jj;
-            const int64_t gr = r0 + lk, gc = c0 + lj;
+            const int64_t gr = r0 + lk, gc = c0 + lj;  // element (gr, gc) of op(B)
             const bool ok = lk < d.hk && lj < d.hn && gr < d.b_rows && gc < d.b_cols;
-            cp_async8(rb + t * BK * BN + e, ok ? d.B + gr * d.ldb + gc : d.B, ok ? 8 : 0);
+            const double* src = d.trans_b ? d.B + gc * d.ldb + gr : d.B + gr * d.ldb + gc;
+            cp_async8(rb + t * BK * BN + e, ok ? src : d.B, ok ? 8 : 0);
           }
         }
         cp_async_mbar_arrive(&raw_full[slot]);
@@ -463,24 +473,37 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       constexpr int EPT = BM * BK / kProducers;
       static_assert(BM == BN && EPT * kProducers == BM * BK && EPT % 2 == 0, "producer element mapping");
       const int pr = pt % BM, koff = (pt / BM) * EPT;
+      // Raw tiles of A^T and B^T arrive k-major ([BK][BM]) and column-major ([BN][BK]):
+      // the same element (row pr, k koff + i) is then read with the other strides.
       {
         uint64_t v[EPT];
         const uint64_t s0 = (uint64_t)term_neg(c_plans.ta[row][0]) << 63;
-        const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(ra + pr * BK + koff);
-#pragma unroll
-        for (int h = 0; h < EPT / 2; ++h) {
-          const ulonglong2 w = r0[h];
-          v[2 * h] = w.x ^ s0;
-          v[2 * h + 1] = w.y ^ s0;
-        }
-        for (int t = 1; t < na; ++t) {
-          const uint64_t st = (uint64_t)term_neg(c_plans.ta[row][t]) << 63;
-          const ulonglong2* rt = reinterpret_cast<const ulonglong2*>(ra + t * BM * BK + pr * BK + koff);
+        if (!d.trans_a) {
+          const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(ra + pr * BK + koff);
 #pragma unroll
           for (int h = 0; h < EPT / 2; ++h) {
-            const ulonglong2 w = rt[h];
-            v[2 * h] = int_fadd_bits(v[2 * h], w.x ^ st);
-            v[2 * h + 1] = int_fadd_bits(v[2 * h + 1], w.y ^ st);
+            const ulonglong2 w = r0[h];
+            v[2 * h] = w.x ^ s0;
+            v[2 * h + 1] = w.y ^ s0;
+          }
+          for (int t = 1; t < na; ++t) {
+            const uint64_t st = (uint64_t)term_neg(c_plans.ta[row][t]) << 63;
+            const ulonglong2* rt = reinterpret_cast<const ulonglong2*>(ra + t * BM * BK + pr * BK + koff);
+#pragma unroll
+            for (int h = 0; h < EPT / 2; ++h) {
+              const ulonglong2 w = rt[h];
+              v[2 * h] = int_fadd_bits(v[2 * h], w.x ^ st);
+              v[2 * h + 1] = int_fadd_bits(v[2 * h + 1], w.y ^ st);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < EPT; ++i) v[i] = ra[(koff + i) * BM + pr] ^ s0;
+          for (int t = 1; t < na; ++t) {
+            const uint64_t st = (uint64_t)term_neg(c_plans.ta[row][t]) << 63;
+            const uint64_t* rt = ra + t * BM * BK + pr;
+#pragma unroll
+            for (int i = 0; i < EPT; ++i) v[i] = int_fadd_bits(v[i], rt[(koff + i) * BM] ^ st);
           }
         }
 #pragma unroll
@@ -489,13 +512,33 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       {
         uint64_t v[EPT];
         const uint64_t s0 = (uint64_t)term_neg(c_plans.tb[row][0]) << 63;
+        if (!d.trans_b) {
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) v[i] = rb[(koff + i) * BN + pr] ^ s0;
-        for (int t = 1; t < nb; ++t) {
-          const uint64_t st = (uint64_t)term_neg(c_plans.tb[row][t]) << 63;
-          const uint64_t* rt = rb + t * BK * BN + pr;
+          for (int i = 0; i < EPT; ++i) v[i] = rb[(koff + i) * BN + pr] ^ s0;
+          for (int t = 1; t < nb; ++t) {
+            const uint64_t st = (uint64_t)term_neg(c_plans.tb[row][t]) << 63;
+            const uint64_t* rt = rb + t * BK * BN + pr;
 #pragma unroll
-          for (int i = 0; i < EPT; ++i) v[i] = int_fadd_bits(v[i], rt[(koff + i) * BN] ^ st);
+            for (int i = 0; i < EPT; ++i) v[i] = int_fadd_bits(v[i], rt[(koff + i) * BN] ^ st);
+          }
+        } else {
+          const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(rb + pr * BK + koff);
+#pragma unroll
+          for (int h = 0; h < EPT / 2; ++h) {
+            const ulonglong2 w = r0[h];
+            v[2 * h] = w.x ^ s0;
+            v[2 * h + 1] = w.y ^ s0;
+          }
+          for (int t = 1; t < nb; ++t) {
+            const uint64_t st = (uint64_t)term_neg(c_plans.tb[row][t]) << 63;
+            const ulonglong2* rt = reinterpret_cast<const ulonglong2*>(rb + t * BK * BN + pr * BK + koff);
+#pragma unroll
+            for (int h = 0; h < EPT / 2; ++h) {
+              const ulonglong2 w = rt[h];
+              v[2 * h] = int_fadd_bits(v[2 * h], w.x ^ st);
+              v[2 * h + 1] = int_fadd_bits(v[2 * h + 1], w.y ^ st);
+            }
+          }
         }
 #pragma unroll
         for (int i = 0; i < EPT; ++i) sb[(koff + i) * BN + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
@@ -583,6 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       const int nc = d.m_target ? 1 : (int)c_plans.nc[row];
       const int tm = m.t / d.tiles_n, tn = m.t - (m.t / d.tiles_n) * d.tiles_n;
       const int warp = tid >> 5, lane = tid & 31;
+      const double alpha = d.alpha;  // exact no-op for alpha = 1
       double* stage = epi_stage + warp * (2 * BN);
       const int half = ty - 2 * warp;  // which of the warp's two thread rows
 #pragma unroll
@@ -591,8 +635,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
         double2* dst1 = reinterpret_cast<double2*>(stage + half * BN + BN / 2 + tx * (TN / 2));
 #pragma unroll
         for (int v = 0; v < TN / 4; ++v) {
-          dst0[v] = make_double2(acc[i][2 * v], acc[i][2 * v + 1]);
-          dst1[v] = make_double2(acc[i][TN / 2 + 2 * v], acc[i][TN / 2 + 2 * v + 1]);
+          dst0[v] = make_double2(alpha * acc[i][2 * v], alpha * acc[i][2 * v + 1]);
+          dst1[v] = make_double2(alpha * acc[i][TN / 2 + 2 * v], alpha * acc[i][TN / 2 + 2 * v + 1]);
         }
         __syncwarp();
         // Local tile rows of this row group for the warp's two thread rows.
@@ -746,12 +790,23 @@ void fill_desc(const Fp64Launch& L, ProbDesc* d) {
   d->tiles_m = (int)((L.hm + BT - 1) / BT);
   d->tiles_n = (int)((L.hn + BT - 1) / BT);
   d->ksteps = (int)((L.hk + BK - 1) / BK);
+  d->trans_a = L.trans_a;
+  d->trans_b = L.trans_b;
+  d->alpha = L.alpha;
+  // The innermost TMA coordinate is a block offset along k (A), n (B), m (A^T) or k
+  // (B^T) plus a multiple of the tile: those block edges must be even.
+  const bool edges_even = L.levels == 0 || (L.hk % 2 == 0 && L.hn % 2 == 0 && (!L.trans_a || L.hm % 2 == 0));
   const bool aligned = ((uintptr_t)L.A % 16 == 0) && ((uintptr_t)L.B % 16 == 0) && (L.lda % 2 == 0) &&
-                       (L.ldb % 2 == 0) && (L.levels == 0 || (L.hk % 2 == 0 && L.hn % 2 == 0)) &&
+                       (L.ldb % 2 == 0) && edges_even &&
                        L.a_cols < (1LL << 31) && L.a_rows < (1LL << 31) && L.b_cols < (1LL << 31) &&
                        L.b_rows < (1LL << 31);
-  d->use_tma = aligned && encode_2d(&d->tmA, L.A, L.a_rows, L.a_cols, L.lda, BK, BT) &&
-               encode_2d(&d->tmB, L.B, L.b_rows, L.b_cols, L.ldb, BT, BK);
+  // Tensor maps over the stored matrices: A (m x k) or A^T's storage (k x m), B (k x n)
+  // or B^T's storage (n x k).
+  const bool ma = L.trans_a ? encode_2d(&d->tmA, L.A, L.a_cols, L.a_rows, L.lda, BT, BK)
+                            : encode_2d(&d->tmA, L.A, L.a_rows, L.a_cols, L.lda, BK, BT);
+  const bool mb = L.trans_b ? encode_2d(&d->tmB, L.B, L.b_cols, L.b_rows, L.ldb, BK, BT)
+                            : encode_2d(&d->tmB, L.B, L.b_rows, L.b_cols, L.ldb, BT, BK);
+  d->use_tma = aligned && ma && mb;
 }
 
 }  // namespace

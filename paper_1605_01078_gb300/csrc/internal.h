@@ -61,6 +61,8 @@ struct Fp64Launch {
   EpilogueKind epi;
   ScheduleKind sched;
   int tile;                // 0: 128 x 128 block tile, 1: 64 x 64, -1: the library's choice
+  int trans_a, trans_b;    // op(A) = A^T (A stored k x m, ld >= m); op(B) = B^T (stored n x k)
+  double alpha;            // C += alpha * (product); 1 for the plain operation
 };
 
 // Fills the fields common to a full-operand launch.
@@ -108,14 +110,17 @@ int fp64_device_status(cudaStream_t stream);
 
 // Naive / AB helpers (elementwise.cu).
 // dst (rows x cols, ld = cols) = sum_t sign_t * block_t of src, masked to src's extent.
+// With trans, src holds the transpose (element (r, c) at src[c * ld + r]).
 cudaError_t launch_block_sum(double* dst, int64_t rows, int64_t cols,
                              const double* src, int64_t ld, int64_t src_rows, int64_t src_cols,
                              int64_t h_r, int64_t h_c, const uint8_t* terms, int nterms,
-                             cudaStream_t stream);
-// For each target t: C block (bi, bj) += sign * M (hm x hn, ld = hn), masked to C.
+                             cudaStream_t stream, int trans = 0);
+// For each target t: C block (bi, bj) += sign * alpha * M (hm x hn, ld = hn), masked to C.
 cudaError_t launch_combine(double* C, int64_t ldc, int64_t c_rows, int64_t c_cols,
                            const double* M, int64_t hm, int64_t hn,
-                           const uint8_t* targets, int ntargets, cudaStream_t stream);
+                           const uint8_t* targets, int ntargets, cudaStream_t stream, double alpha = 1.0);
+// C (rows x cols, ldc) = beta C; beta = 0 writes zeros without reading C; beta = 1 is a no-op.
+cudaError_t launch_scale(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta, cudaStream_t stream);
 
 int device_sm_count();
 
@@ -124,7 +129,8 @@ int device_sm_count();
 // the read-and-clear of its device status word.
 int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels);
 cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                      double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream);
+                      double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream, int trans_a = 0,
+                      int trans_b = 0, double alpha = 1.0);
 int ozaki_device_status();
 
 // Learned selector (mlp.cu): argmin of the loaded MLP's predictions for a shape;

@@ -119,14 +119,15 @@ __device__ __forceinline__ unsigned long long mag_bits(unsigned long long bits) 
 // extent, formed with the integer-pipe addition (no floating-point instruction).
 __device__ __forceinline__ unsigned long long operand_sum(const double* src, int64_t ld, int64_t rows,
                                                           int64_t cols, int64_t h_r, int64_t h_c,
-                                                          const uint8_t* terms, int nterms, int64_t r, int64_t c) {
+                                                          const uint8_t* terms, int nterms, int64_t r, int64_t c,
+                                                          int trans) {
   const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
   unsigned long long v = 0;
   for (int t = 0; t < nterms; ++t) {
     const uint8_t code = terms[t];
     const int64_t gr = (int64_t)term_bi(code) * h_r + r, gc = (int64_t)term_bj(code) * h_c + c;
     unsigned long long x = 0;
-    if (r < h_r && c < h_c && gr < rows && gc < cols) x = s64[gr * ld + gc];
+    if (r < h_r && c < h_c && gr < rows && gc < cols) x = trans ? s64[gc * ld + gr] : s64[gr * ld + gc];
     x ^= (unsigned long long)term_neg(code) << 63;
     v = t == 0 ? x : int_fadd_bits(v, x);
   }
@@ -142,6 +143,7 @@ struct SplitArgs {
   int64_t h_out, h_outp;    // output rows (h_m or h_n) and padded rows
   int64_t h_k, h_kp;        // reduction length and padded length
   int plan_off;             // table row of product 0
+  int trans;                // the source is stored transposed (element (r, c) at src[c * ld + r])
   __nv_bfloat16* slices;    // [P][S][h_outp][h_kp]
   int* exps;                // [P][h_outp]
 };
@@ -166,7 +168,7 @@ __global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
   }
   unsigned long long mx = 0;
   for (int64_t k = threadIdx.x; k < a.h_k; k += blockDim.x) {
-    const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, i, k);
+    const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, i, k, a.trans);
     rowbuf[k] = x;
     mx = max(mx, mag_bits(x));
   }
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256) oz_colmax(const __grid_constant__ SplitAr
   unsigned long long mx = 0;
   if (j0 + c < a.h_out)
     for (int64_t k = kb + ph; k < ke; k += 4)
-      mx = max(mx, mag_bits(operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j0 + c)));
+      mx = max(mx, mag_bits(operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j0 + c, a.trans)));
   red[ph][c] = mx;
   __syncthreads();
   if (tid < 64) {
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ Spl
       float d[kS];
       long long N = 0;
       if (j < a.h_out && k < a.h_k) {
-        const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j);
+        const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j, a.trans);
         N = scaled_rint(x, ecol[cc]);
       }
       digits_of(N, d);
@@ -551,6 +553,7 @@ struct RecombineArgs {
   int64_t hm, hn, h_mp, h_np;
   int levels, P;
   int plan_off;   // table row of product 0 of the level
+  double alpha;   // C_q += gamma_q alpha M
   const int* G;   // [nseg][P][kGroups][h_mp][h_np]
   int nseg;
   const int* e;   // [P][h_mp]
@@ -647,7 +650,8 @@ __global__ void oz_recombine_scatter(const __grid_constant__ RecombineArgs a) {
         }
         const double M = round_i128(th, tl,
                                     a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
-        c = term_neg(code) ? c - M : c + M;
+        const double aM = a.alpha * M;  // exact for alpha = 1
+        c = term_neg(code) ? c - aM : c + aM;
       }
     }
     a.C[gr * a.ldc + gc] = c;
@@ -712,7 +716,8 @@ int ozaki_device_status() {
 }
 
 cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                      double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream) {
+                      double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream, int trans_a, int trans_b,
+                      double alpha) {
   std::call_once(g_oz_once, oz_init);
   if (g_oz_init != cudaSuccess) return g_oz_init;
   int sms = device_sm_count();
@@ -733,7 +738,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   SplitArgs sa;
   sa.src = A; sa.ld = lda; sa.rows = m; sa.cols = k; sa.h_r = hm; sa.h_c = hk;
   sa.h_out = hm; sa.h_outp = hmp; sa.h_k = hk; sa.h_kp = hkp;
-  sa.plan_off = kPlanOffset[levels]; sa.slices = DX; sa.exps = ex;
+  sa.plan_off = kPlanOffset[levels]; sa.slices = DX; sa.exps = ex; sa.trans = trans_a;
   const size_t row_smem = (size_t)hk * sizeof(double);
   if (row_smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)oz_split_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -747,7 +752,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   SplitArgs sb;
   sb.src = B; sb.ld = ldb; sb.rows = k; sb.cols = n; sb.h_r = hk; sb.h_c = hn;
   sb.h_out = hn; sb.h_outp = hnp; sb.h_k = hk; sb.h_kp = hkp;
-  sb.plan_off = kPlanOffset[levels]; sb.slices = DV; sb.exps = fx;
+  sb.plan_off = kPlanOffset[levels]; sb.slices = DV; sb.exps = fx; sb.trans = trans_b;
   e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)P * hnp, stream);
   if (e != cudaSuccess) return e;
   oz_colmax<<<dim3((unsigned)(hnp / 64), (unsigned)((hk + kColMaxRows - 1) / kColMaxRows), (unsigned)P), 256, 0,
@@ -780,7 +785,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   ra.C = C; ra.ldc = ldc; ra.m = m; ra.n = n;
   ra.hm = hm; ra.hn = hn; ra.h_mp = hmp; ra.h_np = hnp;
   ra.levels = levels; ra.P = P; ra.plan_off = kPlanOffset[levels];
-  ra.G = G; ra.nseg = nseg; ra.e = ex; ra.f = fx;
+  ra.G = G; ra.nseg = nseg; ra.e = ex; ra.f = fx; ra.alpha = alpha;
   const int64_t total = hm * hn * (1LL << (2 * levels));
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)sms * 32);

@@ -41,6 +41,9 @@ Fp64Launch make_launch(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   L.epi = kEpiAtomicAdd;
   L.sched = kSchedStreamK;
   L.tile = -1;  // chosen by choose_fp64_schedule / launch_fp64
+  L.trans_a = 0;
+  L.trans_b = 0;
+  L.alpha = 1.0;
   return L;
 }
 

@@ -115,3 +115,16 @@ def test_analytic_model_counts():
     assert f(n, n, n, 2, sg.STRASSEN_NAIVE) > t2
     assert f(256, 256, 256, 2, sg.STRASSEN_NAIVE) > f(256, 256, 256, 0, sg.STRASSEN_ABC)
     assert f(0, 4, 4, 1, 0) == -1.0
+
+
+def test_dgemm_argument_checks_on_the_host():
+    """strassen_dgemm rejects bad transposes, leading dimensions that do not cover the
+    stored (transposed) operands, and overlaps, before any CUDA work."""
+    f = sg.strassen_dgemm
+    assert f(2, 0, 8, 4, 4, 1.0, P, 8, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 0) == -9
+    assert f(1, 0, 8, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 0) == -2   # A^T is 4 x 8: lda >= 8
+    assert f(0, 1, 8, 4, 6, 1.0, P, 6, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 0) == -2   # B^T is 4 x 6: ldb >= 6
+    assert f(0, 0, 4, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, P + 8, 4, 1, 0, 0, 0) == -9   # C overlaps A
+    assert f(0, 0, -1, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 0) == -1
+    assert f(0, 0, 0, 4, 4, 1.0, 0, 4, 0, 4, 1.0, 0, 4, 1, 0, 0, 0) == 0             # empty: no-op
+    assert f(0, 0, 4, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 5, 0, 0, 0) == -4

@@ -286,3 +286,34 @@ def test_dot2_against_exact_rationals():
 def test_max_rel_err_definition():
     A, B = np.array([[2.0, -4.0]]), np.array([[0.5], [3.0]])
     assert oracle.max_rel_err(np.array([[1.0]]), np.array([[0.0]]), A, B) == 1.0 / 12.0
+
+
+# ---------------------------------------------------------------- BLAS semantics (Section 2.2)
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_dgemm_definition_on_integers(ta, tb):
+    """alpha op(A) op(B) + beta C against brute-force triple loops on integers."""
+    m, n, k = 7, 5, 6
+    A = W.integer(k, m, 1) if ta else W.integer(m, k, 1)
+    B = W.integer(n, k, 2) if tb else W.integer(k, n, 2)
+    C = W.integer(m, n, 3)
+    got = oracle.dgemm(ta, tb, 3.0, A, B, -2.0, C)
+    for i in range(m):
+        for j in range(n):
+            acc = 0.0
+            for p in range(k):
+                a = A[p, i] if ta else A[i, p]
+                b = B[j, p] if tb else B[p, j]
+                acc += a * b
+            assert got[i, j] == 3.0 * acc - 2.0 * C[i, j]
+
+
+def test_dgemm_reduces_to_gemm_and_respects_beta_zero():
+    A, B, C = W.integer(9, 4, 4), W.integer(4, 8, 5), W.integer(9, 8, 6)
+    ref = C.copy()
+    oracle.gemm(A, B, ref)
+    assert np.array_equal(oracle.dgemm(0, 0, 1.0, A, B, 1.0, C), ref)
+    Cnan = np.full((9, 8), np.nan)
+    assert np.array_equal(oracle.dgemm(0, 0, 1.0, A, B, 0.0, Cnan), A @ B)
+    assert np.array_equal(oracle.dgemm(1, 1, 2.0, A.T.copy(), B.T.copy(), 0.0, Cnan), 2 * (A @ B))
+    assert np.array_equal(oracle.dgemm(0, 0, 0.0, A, B, 0.5, C), 0.5 * C)
