@@ -558,6 +558,10 @@ struct RecombineArgs {
   int nseg;
   const int* e;   // [P][h_mp]
   const int* f;   // [P][h_np]
+  // The products that update C block q (= qi 2^L + qj), in table order: entries
+  // [first[q], first[q + 1]) of `upd`, each 2 r + (gamma < 0).
+  int first[kMaxTerms * kMaxTerms + 1];
+  uint16_t upd[1728];  // 12^3: the C updates of the deepest table
 };
 
 // RN(T) * 2^scale for the 128-bit two's complement integer T = th * 2^64 + tl, with
@@ -613,48 +617,77 @@ __device__ double round_i128(long long th, unsigned long long tl, int scale) {
   return neg ? -v : v;
 }
 
-__global__ void oz_recombine_scatter(const __grid_constant__ RecombineArgs a) {
-  const int Pn = 1 << a.levels;
-  const int64_t per_block = a.hm * a.hn;
-  const int64_t total = per_block * Pn * Pn;
-  const int off = a.plan_off;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx / per_block);
-    const int64_t rem = idx - (int64_t)q * per_block;
-    const int64_t i = rem / a.hn, j = rem - (rem / a.hn) * a.hn;
-    const int qi = q / Pn, qj = q - (q / Pn) * Pn;
-    const int64_t gr = (int64_t)qi * a.hm + i, gc = (int64_t)qj * a.hn + j;
-    if (gr >= a.m || gc >= a.n) continue;
-    double c = a.C[gr * a.ldc + gc];
-    for (int r = 0; r < a.P; ++r) {
-      const int row = off + r;
-      const int nc = c_oz_plans.nc[row];
-      for (int t = 0; t < nc; ++t) {
-        const uint8_t code = c_oz_plans.tc[row][t];
-        if (term_bi(code) != qi || term_bj(code) != qj) continue;
-        // T = sum_w G_w 2^(b (S + 1 - w)), by Horner over w in 128-bit integers.
-        long long th = 0;
-        unsigned long long tl = 0;
-        const int64_t plane = a.h_mp * a.h_np;
-        const int* g = a.G + (int64_t)r * kGroups * plane + i * a.h_np + j;
+// T = sum_w G_w 2^(b (S + 1 - w)) of product r at (i, j), summed over the k segments,
+// as a 128-bit two's complement integer (th, tl).
+__device__ __forceinline__ void group_total(const RecombineArgs& a, int r, int64_t i, int64_t j, long long* th_out,
+                                            unsigned long long* tl_out) {
+  const int64_t plane = a.h_mp * a.h_np;
+  const int* g = a.G + (int64_t)r * kGroups * plane + i * a.h_np + j;
+  const int64_t seg_stride = (int64_t)a.P * kGroups * plane;
+  long long gw[kGroups];
 #pragma unroll
-        for (int w = 0; w < kGroups; ++w) {
-          th = (long long)(((unsigned long long)th << kB) | (tl >> (64 - kB)));
-          tl <<= kB;
-          long long gw = 0;
-          for (int sg = 0; sg < a.nseg; ++sg) gw += g[((int64_t)sg * a.P * kGroups + w) * plane];
-          const unsigned long long nl = tl + (unsigned long long)gw;
-          th += (gw >> 63) + (nl < tl ? 1 : 0);
-          tl = nl;
+  for (int w = 0; w < kGroups; ++w) {
+    long long v = g[(int64_t)w * plane];
+    for (int sg = 1; sg < a.nseg; ++sg) v += g[sg * seg_stride + (int64_t)w * plane];
+    gw[w] = v;
+  }
+  if (a.nseg <= 128) {
+    // |G_w| < 128 * 2^31: T_hi = G_2 2^16 + G_3 2^8 + G_4 and
+    // T_lo = G_5 2^24 + G_6 2^16 + G_7 2^8 + G_8 fit in int64; T = T_hi 2^32 + T_lo.
+    const long long t_hi = gw[0] * (1LL << 16) + gw[1] * (1LL << 8) + gw[2];
+    const long long t_lo = gw[3] * (1LL << 24) + gw[4] * (1LL << 16) + gw[5] * (1LL << 8) + gw[6];
+    long long th = t_hi >> 32;
+    unsigned long long tl = (unsigned long long)t_hi << 32;
+    const unsigned long long nl = tl + (unsigned long long)t_lo;
+    th += (t_lo >> 63) + (nl < tl ? 1 : 0);
+    *th_out = th;
+    *tl_out = nl;
+    return;
+  }
+  long long th = 0;  // Horner over w in 128-bit integers
+  unsigned long long tl = 0;
+#pragma unroll
+  for (int w = 0; w < kGroups; ++w) {
+    th = (long long)(((unsigned long long)th << kB) | (tl >> (64 - kB)));
+    tl <<= kB;
+    const unsigned long long nl = tl + (unsigned long long)gw[w];
+    th += (gw[w] >> 63) + (nl < tl ? 1 : 0);
+    tl = nl;
+  }
+  *th_out = th;
+  *tl_out = tl;
+}
+
+// One block per C row (grid-stride): for every block column qj the products that
+// update C block (qi, qj) are added in table order, gamma alpha RN(T) 2^(e_i + f_j - 64)
+// each; the threads of the block take consecutive columns.
+__global__ void __launch_bounds__(256) oz_recombine_scatter(const __grid_constant__ RecombineArgs a) {
+  static_assert(kGroups == 7 && kB == 8, "the two-word split of T assumes seven 8-bit groups");
+  const int Pn = 1 << a.levels;
+  for (int64_t gr = blockIdx.x; gr < a.m; gr += gridDim.x) {
+    const int qi = (int)(gr / a.hm);
+    const int64_t i = gr - (int64_t)qi * a.hm;
+    for (int qj = 0; qj < Pn; ++qj) {
+      const int q = qi * Pn + qj;
+      const int u0 = a.first[q], u1 = a.first[q + 1];
+      const int64_t c0 = (int64_t)qj * a.hn;
+      const int64_t cols = (c0 + a.hn < a.n ? c0 + a.hn : a.n) - c0;
+      for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
+        double* cp = a.C + gr * a.ldc + c0 + j;
+        double c = *cp;
+        for (int u = u0; u < u1; ++u) {
+          const int r = a.upd[u] >> 1;
+          long long th;
+          unsigned long long tl;
+          group_total(a, r, i, j, &th, &tl);
+          const double M = round_i128(th, tl,
+                                      a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
+          const double aM = a.alpha * M;  // exact for alpha = 1
+          c = (a.upd[u] & 1) ? c - aM : c + aM;
         }
-        const double M = round_i128(th, tl,
-                                    a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
-        const double aM = a.alpha * M;  // exact for alpha = 1
-        c = term_neg(code) ? c - aM : c + aM;
+        *cp = c;
       }
     }
-    a.C[gr * a.ldc + gc] = c;
   }
 }
 
@@ -786,9 +819,24 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   ra.hm = hm; ra.hn = hn; ra.h_mp = hmp; ra.h_np = hnp;
   ra.levels = levels; ra.P = P; ra.plan_off = kPlanOffset[levels];
   ra.G = G; ra.nseg = nseg; ra.e = ex; ra.f = fx; ra.alpha = alpha;
-  const int64_t total = hm * hn * (1LL << (2 * levels));
+  // C-update lists per C block, products in table order.
+  {
+    const int Pn = 1 << levels;
+    int n_upd = 0;
+    for (int q = 0; q < Pn * Pn; ++q) {
+      ra.first[q] = n_upd;
+      for (int r = 0; r < P; ++r) {
+        const int row = kPlanOffset[levels] + r;
+        for (int t = 0; t < kPlanTables.nc[row]; ++t) {
+          const uint8_t code = kPlanTables.tc[row][t];
+          if (term_bi(code) * Pn + term_bj(code) == q) ra.upd[n_upd++] = (uint16_t)(2 * r + term_neg(code));
+        }
+      }
+    }
+    ra.first[Pn * Pn] = n_upd;
+  }
   const int threads = 256;
-  const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, (int64_t)sms * 32);
+  const int64_t blocks = std::min<int64_t>(m, (int64_t)sms * 8);
   oz_recombine_scatter<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, stream>>>(ra);
   return cudaGetLastError();
 }
