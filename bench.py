@@ -24,7 +24,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import os
 import statistics
@@ -139,6 +138,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# The sources the FP64 product kernel is compiled from (its recorded traffic is valid
+# only while they are unchanged).
+KERNEL_SOURCES = ("fp64_gemm.cu", "int_fadd.h", "plan_tables.h")
+
+
+def kernel_source_sha256():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1605_01078_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the FP64 product kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
@@ -150,10 +161,7 @@ def recorded_traffic():
         if "=" in line and not line.startswith("#"):
             a, b = line.split("=", 1)
             rec[a.strip()] = b.strip()
-    h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1605_01078_gb300", "csrc", "fp64_gemm.cu"))):
-        h.update(open(f, "rb").read())
-    if rec.get("kernel_source_sha256") != h.hexdigest():
+    if rec.get("kernel_source_sha256") != kernel_source_sha256():
         return None
     try:
         return float(rec["dram_bytes_per_launch_8192_2L_ABC"])
