@@ -1,27 +1,32 @@
 // FP64 product kernel: the general operation of Eq. 4 on GB300.
 //
-// One persistent launch runs every product M_r of one or more problems (Figure 1 /
-// Figure 2 tables) over work units (problem, product r, 128x128 output tile of the
-// block, k-steps of 8).  Each thread block is warp-specialised:
+// One persistent launch runs every product M_r of one or more problems (the Figure 1
+// table, its Kronecker square of Figure 2, or its cube) over work units (problem,
+// product r, BT x BT output tile of the block, k-steps of 8), BT = 128 or 64.  Each
+// thread block is warp-specialised:
 //
-//   producer warps (4)  stage the 1..4 source tiles of A (blocks X_s) and of B
+//   producer warps (4)  stage the 1..8 source tiles of A (blocks X_s) and of B
 //       (blocks V_t) of a k-step into a shared-memory ring -- with TMA box loads
 //       (cp.async.bulk.tensor, completion on an mbarrier) when the operands are
-//       16-byte aligned, else with zero-filling 8-byte cp.async -- and form the
-//       operand sums sum_s delta_s X_s and sum_t eps_t V_t into a ring of "summed"
-//       tiles: the packing-time sums of Section 3.4, with no temporary in global
-//       memory.  Columns past the block edge h_k read as zero (the zero padding of
-//       Section 3.3); TMA zero-fills past the matrix edge.
+//       16-byte aligned, else with zero-filling 8-byte cp.async; transposed operands
+//       with the other box orientation -- and form the operand sums
+//       sum_s delta_s X_s and sum_t eps_t V_t into a ring of "summed" tiles: the
+//       packing-time sums of Section 3.4, with no temporary in global memory.
+//       Columns past the block edge h_k read as zero (the zero padding of Section
+//       3.3); TMA zero-fills past the matrix edge.
 //   consumer warps (8)  accumulate M_tile += A_sum * B_sum with FP64 fused
-//       multiply-adds on an 8x8 register tile per thread and, after the last k-step of
-//       a unit, add gamma_q * M_tile into every C block q the product updates -- the
-//       fused scatter of the micro-kernel (Section 3.4).
+//       multiply-adds on a (BT/16) x (BT/16) register tile per thread and, after the
+//       last k-step of a unit, add gamma_q * alpha * M_tile into every C block q the
+//       product updates -- the fused scatter of the micro-kernel (Section 3.4).
 //
 // C updates are device atomics (red.global.add.f64) for every schedule; a store into a
 // temporary is a clear followed by adds.  The two groups hand tiles over through
-// mbarriers; every wait is bounded (about one
-// second of clock cycles), after which the kernel records STRASSEN_ERR_TIMEOUT in a
-// device status word and returns instead of hanging.
+// mbarriers, with each summed slot's (problem, product, tile, last step) in shared
+// memory; every wait is bounded (about one second of clock cycles), after which the
+// kernel records STRASSEN_ERR_TIMEOUT in a device status word and returns instead of
+// hanging.  A single launch gives each block one stream-K range (or its tiles under
+// the owner schedule); a batched launch lets blocks claim chunks of the stream-K space
+// from a global counter.
 //
 // GB300 design notes.  FP64 runs at about 2 FMA lanes per clock per SM (measured
 // 1.20 TFLOP/s for the whole GPU; DMMA is slower at 1.06), so this kernel is bound by
