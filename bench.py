@@ -323,6 +323,23 @@ def cpu_oracle_effective(n, levels, reps=1):
     return 2.0 * n ** 3 / best / 1e9, best
 
 
+def max_over_ranks(seconds, dist, device):
+    """The slowest rank's time (all ranks call it; without a process group, the local
+    time)."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gflops(flops_per_step, steps, world, seconds):
+    """Whole-job throughput of N replicas: every rank does `steps` steps of
+    `flops_per_step`; the job takes the slowest rank's `seconds`."""
+    return flops_per_step * steps * world / seconds / 1e9
+
+
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
@@ -410,12 +427,9 @@ def main():
     clk = clocks.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     per_launch = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     eff_flops = 2.0 * m * n * k
-    value = eff_flops * args.steps * ws / elapsed / 1e9
+    value = job_gflops(eff_flops, args.steps, ws, elapsed)
 
     # Comparator: the library's classical kernel on the same inputs.
     cls_steps = max(2, args.steps // 3)
@@ -452,12 +466,8 @@ def main():
             e2e_step()
         x1.record(stream)
         barrier()
-        et = x0.elapsed_time(x1) / 1e3
-        if dist is not None:
-            t = torch.tensor([et], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": eff_flops * e_steps * ws / et / 1e9, "unit": UNIT,
+        et = max_over_ranks(x0.elapsed_time(x1) / 1e3, dist, "cuda")
+        e2e = {"value": job_gflops(eff_flops, e_steps, ws, et), "unit": UNIT,
                "h2d_bytes_per_step": int(3 * 8 * m * n), "d2h_bytes_per_step": int(8 * m * n)}
         del dA, dB, dC
 
