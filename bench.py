@@ -232,7 +232,8 @@ def bench_batched(sg, W, torch, reps=3):
 
 def bench_split_precision(sg, W, torch, n=8192, err_n=4096, reps=3):
     """Split-precision FP64 emulation (BF16 digit slices on the tensor cores): effective
-    GFLOP/s at n^3 for 0, 1, 2 levels, and the max-norm error against the library's
+    GFLOP/s at n^3 for 0, 1, 2 levels and at (2n)^3 for level 0, and the max-norm error
+    against the library's
     plain FP64 classical result (normwise: / (||A||_inf max|B|)) for inputs
     u * 2^round(N(0, sigma)) at err_n^3."""
     out = {"workload": f"m=n=k={n} FP64 via BF16 slices, A,B,C uniform[-1,1]", "levels": {}}
@@ -248,6 +249,19 @@ def bench_split_precision(sg, W, torch, n=8192, err_n=4096, reps=3):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / reps
         out["levels"][str(L)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3}
+    del A, B, C
+    # the larger square size of the split-precision workload, classical slices
+    n2 = 2 * n
+    A, B, C = W.uniform_device(n2, n2, 14), W.uniform_device(n2, n2, 15), W.uniform_device(n2, n2, 16)
+    sg.gemm(A, B, C, levels=0, dtype="oz_bf16")
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        sg.gemm(A, B, C, levels=0, dtype="oz_bf16")
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    out[f"n{n2}_level0"] = {"value": 2.0 * n2 ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3}
     del A, B, C
     errs = {}
     for sigma in (0, 4, 10):
