@@ -489,8 +489,15 @@ def main():
     if args.dtype == "f64" and rank == 0 and m <= 8192:
         err_headline = level_error(sg, torch, A, B, C, stream, L, variant)
     levels_other = None
+    small = None
     if not args.no_levels and args.dtype == "f64" and rank == 0:
         levels_other = bench_other_levels(sg, torch, A, B, C, stream, [lv for lv in (1, 2, 3) if lv != L])
+        # the small square case: m = n = k = 1024, one-level ABC, C = 0
+        As, Bs = W.uniform_device(1024, 1024, 0), W.uniform_device(1024, 1024, 1)
+        Cs = torch.zeros((1024, 1024), dtype=torch.float64, device="cuda")
+        small = {"workload": "m=n=k=1024, one-level ABC, C = 0 (uniform[-1,1])"}
+        small.update(bench_other_levels(sg, torch, As, Bs, Cs, stream, [1], reps=20)["1"])
+        del As, Bs, Cs
 
     batched = None
     if not args.no_batched and rank == 0:
@@ -549,6 +556,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": e2e,
         "other_levels": levels_other,
+        "small_square": small,
         "batched": batched,
         "split_precision": split,
         "gpu_launches": launches_per_step * args.steps,
