@@ -900,7 +900,7 @@ namespace {
 // descriptors -- TMA tensor maps encoded on the host included -- into the device
 // array the persistent kernel reads.
 constexpr int kDescPerExpand = (32000 - 64) / (int)sizeof(ProbDesc);
-constexpr int kChunksPerBlock = 16;
+constexpr int kChunksPerBlock = 64;
 struct ExpandArgs {
   ProbDesc* out;
   unsigned long long* counter;  // cleared when not null
@@ -989,7 +989,7 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   args.nprob = (int)descs.size();
   args.sched = kSchedStreamK;
   args.total = total;
-  // Chunks of about 1/16 of a block's even share: blocks that meet cheaper iterations
+  // Chunks of about 1/64 of a block's even share: blocks that meet cheaper iterations
   // (fewer C targets per unit, TMA instead of cp.async staging) claim more of them.
   args.chunk = std::max<int64_t>(1, (total + (int64_t)sms * kChunksPerBlock - 1) / ((int64_t)sms * kChunksPerBlock));
   args.nchunks = (total + args.chunk - 1) / args.chunk;
