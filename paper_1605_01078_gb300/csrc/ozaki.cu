@@ -57,6 +57,7 @@ constexpr int kTM = 128, kTN = 256, kTK = 64;  // tile; kTK bf16 = one 128-byte 
 constexpr int kStages = 4;
 constexpr int kChunkItems = 4;   // k-blocks of 64 per exact FP32 chunk: 256 products, |sum| <= 2^22
 constexpr int kSegKB = 256;      // k-blocks per k segment: int32 group sums stay below 2^31
+constexpr int kGroupRows = 16;   // tile rows per group of the unit order (L2 reuse)
 constexpr int kThreads = 384;    // warp 0 TMA, warp 1 MMA + TMEM, warps 4..11 epilogue
 constexpr int kEpiThreads = 256;
 constexpr long long kWaitLimit = 2000000000LL;
@@ -413,13 +414,20 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
 
   const int tiles = a.tiles_m * a.tiles_n;
   const int units = a.P * tiles * a.nseg;
+  // Unit u -> (product, tile, k segment).  Within a product the tiles go in groups of
+  // kGroupRows tile rows, column by column inside a group, so that the units running at
+  // the same time share their A digit rows and B digit columns in the L2.
   auto unit_of = [&](int u, int* p, int* tm, int* tn, int* kb0, int* kb1) {
     const int per_p = tiles * a.nseg;
     *p = u / per_p;
     const int rem = u - *p * per_p;
     const int t = rem / a.nseg, g = rem - (rem / a.nseg) * a.nseg;
-    *tm = t / a.tiles_n;
-    *tn = t - (t / a.tiles_n) * a.tiles_n;
+    const int group = t / (kGroupRows * a.tiles_n);
+    const int first = group * kGroupRows;
+    const int rows = a.tiles_m - first < kGroupRows ? a.tiles_m - first : kGroupRows;
+    const int in = t - group * kGroupRows * a.tiles_n;
+    *tm = first + in % rows;
+    *tn = in / rows;
     *kb0 = g * kSegKB;
     *kb1 = (g + 1) * kSegKB < a.nkb ? (g + 1) * kSegKB : a.nkb;
   };
