@@ -116,6 +116,7 @@ struct KArgs {
   int64_t total;           // stream-K: iterations of all problems; owner: tile positions
   int64_t chunk;           // batched: iterations per claimed chunk
   int64_t nchunks;
+  int64_t dp_rounds;       // single stream-K launch: rounds of whole units before the split tail
 };
 
 // What the producers tell the consumers about the k-step in a summed slot.
@@ -217,8 +218,19 @@ __device__ Cursor range_cursor(const KArgs& a, int64_t id) {
       beg = id * a.chunk;
       end = beg + a.chunk < a.total ? beg + a.chunk : a.total;
     } else {
-      beg = (a.total * id) / gridDim.x;
-      end = (a.total * (id + 1)) / gridDim.x;
+      // Claims 0 .. dp_rounds - 1: whole units, round-robin over the blocks, so the
+      // blocks of one round work on neighbouring tiles of the same product at the same
+      // k (their operand tiles meet in the L2); the last claim: an even share of the
+      // remaining units' iterations (stream-K), which balances the tail.
+      const int64_t ksteps = a.single.ksteps;
+      if (id < a.dp_rounds) {
+        beg = (id * gridDim.x + blockIdx.x) * ksteps;
+        end = beg + ksteps;
+      } else {
+        const int64_t tb = a.dp_rounds * gridDim.x * ksteps, len = a.total - tb;
+        beg = tb + (len * blockIdx.x) / gridDim.x;
+        end = tb + (len * (blockIdx.x + 1)) / gridDim.x;
+      }
     }
     c.left = end - beg;
     if (c.left > 0) {
@@ -349,6 +361,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
         if (pt != 0) mbar_arrive(claim_empty);
         ++nclaims;
         return c < (unsigned long long)a.nchunks ? (int64_t)c : -1;
+      } else if (a.sched == kSchedStreamK) {
+        return nclaims <= a.dp_rounds ? (int64_t)nclaims++ : -1;
       } else {
         return nclaims++ == 0 ? (int64_t)blockIdx.x : -1;
       }
@@ -881,6 +895,7 @@ cudaError_t launch_fp64(const Fp64Launch& L, cudaStream_t stream) {
   if (L.sched == kSchedStreamK) {
     args.total = (int64_t)d.nprod * tiles * d.ksteps;
     grid = std::min<int64_t>(sms, args.total);
+    args.dp_rounds = ((int64_t)d.nprod * tiles) / grid;  // whole-unit rounds; the rest is split
   } else {
     args.total = tiles;
     grid = std::min<int64_t>(sms, tiles);
