@@ -128,3 +128,20 @@ def test_dgemm_argument_checks_on_the_host():
     assert f(0, 0, -1, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 0) == -1
     assert f(0, 0, 0, 4, 4, 1.0, 0, 4, 0, 4, 1.0, 0, 4, 1, 0, 0, 0) == 0             # empty: no-op
     assert f(0, 0, 4, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 5, 0, 0, 0) == -4
+
+
+def test_plain_c_client_compiles_and_runs(tmp_path):
+    """The header is plain C (extern "C", C types only): a C99 program includes it, links
+    the library and calls its host-side entry points."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    sg.load_library()
+    libdir = os.path.dirname(_binding.LIB_PATH)
+    exe = tmp_path / "abi_client"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "native", "abi_client.c"), "-o", str(exe),
+                           "-L", libdir, "-lstrassen_gb300", f"-Wl,-rpath,{libdir}"])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "abi client ok" in r.stdout, r.stdout + r.stderr
