@@ -357,7 +357,8 @@ struct GemmArgs {
   CUtensorMap tmB;  // DV of all products as rows [P*S*h_np] x cols [h_kp], bf16, box 64 x 256
   int* G;           // [nseg][P][kGroups][h_mp][h_np] exact group sums G_w (w = 2 .. kS + 1) per k segment
   int P, tiles_m, tiles_n, nkb;
-  int nseg;         // k segments of kSegKB k-blocks (each segment's sums fit in int32)
+  int nseg;         // k segments of seg_kb <= kSegKB k-blocks (each segment's sums fit in int32)
+  int seg_kb;
   int64_t h_mp, h_np;
 };
 
@@ -428,8 +429,8 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
     const int in = t - group * kGroupRows * a.tiles_n;
     *tm = first + in % rows;
     *tn = in / rows;
-    *kb0 = g * kSegKB;
-    *kb1 = (g + 1) * kSegKB < a.nkb ? (g + 1) * kSegKB : a.nkb;
+    *kb0 = g * a.seg_kb;
+    *kb1 = (g + 1) * a.seg_kb < a.nkb ? (g + 1) * a.seg_kb : a.nkb;
   };
 
   if (warp < 4) {
@@ -535,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
           mbar_arrive(&tempty[buf]);
         }
         if (bad) break;
-        const int seg = kb0 / kSegKB;
+        const int seg = kb0 / a.seg_kb;
         int* dst = a.G + ((((int64_t)seg * a.P + p) * kGroups + (w - 2)) * a.h_mp + row) * a.h_np + col0;
         int4* d4 = reinterpret_cast<int4*>(dst);
 #pragma unroll
@@ -735,13 +736,23 @@ bool encode_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
 
 int64_t round_up(int64_t x, int64_t q) { return (x + q - 1) / q * q; }
 
+// Number of k segments: enough that every segment's int32 group sums stay below 2^31
+// (at most kSegKB k-blocks), and more while the units would make fewer than six waves
+// on the GPU and each segment keeps at least 16 k-blocks (the segments are separate
+// units and balance the waves; the recombination adds them).
+int plan_segments(int64_t units_per_seg, int64_t nkb, int sms) {
+  int64_t nseg = (nkb + kSegKB - 1) / kSegKB;
+  while (units_per_seg * nseg < 6LL * sms && nkb / (nseg + 1) >= 16) ++nseg;
+  return (int)nseg;
+}
+
 }  // namespace
 
 int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
   const int64_t P = kPlanCount[levels];
   const int64_t hmp = round_up(block_edge(m, levels), kTM), hnp = round_up(block_edge(n, levels), kTN),
                 hkp = round_up(block_edge(k, levels), kTK);
-  const int64_t nseg = (hkp / kTK + kSegKB - 1) / kSegKB;
+  const int64_t nseg = plan_segments(P * (hmp / kTM) * (hnp / kTN), hkp / kTK, std::max(device_sm_count(), 1));
   return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + nseg * kGroups * P * hmp * hnp * 4 + P * hnp * 8 +
          4096;
 }
@@ -772,7 +783,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   int* ex = (int*)w;                                           w += (size_t)P * hmp * 4;
   int* fx = (int*)w;                                           w += (size_t)P * hnp * 4;
   w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
-  const int nseg = (int)((hkp / kTK + kSegKB - 1) / kSegKB);
+  const int nseg = plan_segments((int64_t)P * (hmp / kTM) * (hnp / kTN), hkp / kTK, sms);
   int* G = (int*)w;                                            w += (size_t)nseg * kGroups * P * hmp * hnp * 4;
   unsigned long long* colmax = (unsigned long long*)w;  // [P][h_np] magnitude bits
 
@@ -815,6 +826,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   ga.tiles_m = (int)(hmp / kTM); ga.tiles_n = (int)(hnp / kTN);
   ga.nkb = (int)(hkp / kTK);
   ga.nseg = nseg;
+  ga.seg_kb = (int)((ga.nkb + nseg - 1) / nseg);
   ga.h_mp = hmp; ga.h_np = hnp;
   const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n * ga.nseg;
   const int grid = (int)std::min<int64_t>(sms, units);
