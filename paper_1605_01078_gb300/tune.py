@@ -303,6 +303,9 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--out", required=True)
     ap.add_argument("--sweep", action="store_true", help="run the FP64 shape sweep only")
+    ap.add_argument("--evaluate", default=None,
+                    help="a selector JSON (as shipped in data/): measure only the held-out shapes and report "
+                         "the regret of that network, the analytic model and the fixed rules")
     a = ap.parse_args(argv)
     if a.sweep:
         sweep(a.out)
@@ -316,6 +319,28 @@ def main(argv=None) -> int:
     t0 = time.time()
     f64 = B.STRASSEN_F64
     oz = B.STRASSEN_F64_OZ_BF16
+    if a.evaluate:
+        with open(a.evaluate) as fh:
+            params = np.array(json.load(fh)["params"], dtype=np.float32)
+        held_rows = measure(W.loguniform_shapes(a.heldout, 2, a.lo, a.hi), f64, timer)
+        held_oz = measure(W.loguniform_shapes(a.oz_heldout, 4, a.lo, a.hi), oz, timer)
+        summary = {"shapes_heldout_f64": len(held_rows), "shapes_heldout_oz": len(held_oz),
+                   "seconds_measuring": time.time() - t0}
+        for name, rows in (("f64", held_rows), ("oz_bf16", held_oz)):
+            summary[name] = {
+                "mlp": regret(rows, choose_mlp(params, rows)),
+                "analytic_model": regret(rows, choose_model(rows)),
+                "always_1L_ABC": regret(rows, choose_fixed(rows, 1)),
+                "always_2L_ABC": regret(rows, choose_fixed(rows, 4)),
+                "classical": regret(rows, choose_fixed(rows, 0)),
+                "exhaustive": regret(rows, [best_of(r) for r in rows]),
+                "best_counts": {str(c): int(sum(best_of(r) == c for r in rows)) for c in range(7)},
+            }
+        save_rows(os.path.join(a.out, "selector_heldout_rows.json"), held_rows + held_oz)
+        with open(os.path.join(a.out, "selector_evaluation.json"), "w") as fh:
+            json.dump(summary, fh, indent=1)
+        print(json.dumps({k: summary[k] for k in ("f64", "oz_bf16")}, indent=1))
+        return 0
     train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, timer)
     train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, timer)
     t_train = time.time() - t0
