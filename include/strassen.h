@@ -21,7 +21,8 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Operation:  C <- C + A * B  (alpha = beta = 1; the paper reduces DGEMM to
- *             C = alpha*A*B + C in Section 2.2 and this library fixes alpha = 1).
+ *             C = alpha*A*B + C in Section 2.2).  strassen_dgemm adds the full BLAS
+ *             form C = alpha op(A) op(B) + beta C with transposes.
  * Layout:     row-major.  A is m x k with lda >= k, B is k x n with ldb >= n, C is
  *             m x n with ldc >= n; element (i, j) of A is A[i*lda + j].  Column-major
  *             callers pass (B^T, A^T, C^T) with m and n swapped.
@@ -43,6 +44,9 @@
  *             the tensor cores on integer slices of the FP64 operands (see
  *             strassen_dtype) and the scaling, recombination and C accumulation stay
  *             in FP64.
+ * Levels:     0 (classical) to STRASSEN_MAX_LEVELS = 3 (343 products); the FP64 kernel
+ *             picks a 128x128 or 64x64 block tile per call (strassen_select reports
+ *             the tile it would use: tile_id 0 or 1).
  */
 #ifndef STRASSEN_GB300_H
 #define STRASSEN_GB300_H
@@ -206,18 +210,20 @@ STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
 
 /*
  * strassen_select -- the variant selector: picks which member of the family (classical,
- * or 1 / 2 / 3 levels of ABC, AB or Naive; tile_id is always 0, the 128x128x8 tile) to
- * run for an m x n x k product in `dtype` -- the choice Section 4.2 of the paper
- * builds its performance model for.  In order of precedence it returns
+ * or 1 / 2 / 3 levels of ABC, AB or Naive) and which block tile (tile_id 0: 128x128x8,
+ * 1: 64x64x8) to run for an m x n x k product in `dtype` -- the choice Section 4.2 of
+ * the paper builds its performance model for.  In order of precedence it returns
  *   1. the exhaustive-measurement record for exactly this shape and dtype, if one was
  *      stored with strassen_tune_record();
  *   2. the argmin of the learned selector's predictions, if a network was loaded with
  *      strassen_selector_load() (one small kernel launch on a library stream, then a
  *      wait for its result);
- *   3. the analytic model's argmin (strassen_model_seconds, levels 0 to 3) otherwise
+ *   3. the analytic model's argmin over levels 0 to 3, variants and tiles otherwise
  *      (FP64), or classical slices (split-precision dtypes).
  * The learned selector's candidates stop at two levels (its output layer has the 7
- * candidates listed below); exhaustive records may hold any level.
+ * candidates listed below; the tile then follows the analytic model); exhaustive
+ * records may hold any level and tile.  strassen_gemm with levels = -1 and
+ * STRASSEN_AUTO runs exactly the selected (levels, variant, tile).
  * The model prefers fewer levels on ties within 1 %.
  *
  *   levels, variant, tile_id   outputs (host pointers, non-NULL).
@@ -228,9 +234,9 @@ STRASSEN_API int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype
 
 /*
  * strassen_tune_record / strassen_tune_clear -- store (or forget all) exhaustive
- * measurement results: the fastest (levels, variant, tile_id) measured for a shape
- * and dtype, which strassen_select() then returns for exactly that shape.  The table
- * lives in host memory of the process.  Returns STRASSEN_OK or a negative status.
+ * measurement results: the fastest (levels 0-3, variant, tile_id 0 or 1) measured for
+ * a shape and dtype, which strassen_select() then returns for exactly that shape.  The
+ * table lives in host memory of the process.  Returns STRASSEN_OK or a negative status.
  */
 STRASSEN_API int strassen_tune_record(int64_t m, int64_t n, int64_t k, strassen_dtype dtype,
                                       int levels, strassen_variant variant, int tile_id);
@@ -238,10 +244,11 @@ STRASSEN_API int strassen_tune_clear(void);
 
 /*
  * strassen_model_seconds -- the analytic time model (the paper's T = T_a + T_m of
- * Section 4.2, restated for this GPU): FP64 multiply-adds of the padded 128x128x8
- * tiles and the operand-sum and C-update additions at the FP64 pipe rate, the extra
- * temporary passes of AB and Naive at the HBM rate, and a fixed cost per kernel
- * launch.  Returns the predicted seconds, or -1 for invalid arguments.
+ * Section 4.2, restated for this GPU): FP64 multiply-adds of the padded block tiles
+ * (the cheaper of 128x128x8 and 64x64x8) and the additions of Naive's and AB's separate
+ * kernels at the FP64 pipe rate (ABC's and AB's staging sums run on the integer pipe),
+ * the extra temporary passes of AB and Naive at the HBM rate, and a fixed cost per
+ * kernel launch.  Returns the predicted seconds, or -1 for invalid arguments.
  */
 STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int levels,
                                            strassen_variant variant);
