@@ -15,7 +15,6 @@ Contents
 * :mod:`oracle.ozaki` -- error-free splitting of FP64 operands into integer slices
   and their exact products (split-precision emulation).
 * :mod:`oracle.mlp` -- FP64 forward/backward of the variant-selector MLP.
-* :mod:`oracle.model` -- the analytic time model of Section 4.2.
 """
 from __future__ import annotations
 
