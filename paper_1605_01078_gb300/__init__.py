@@ -1,7 +1,7 @@
 """Strassen's algorithm fused into GEMM on GB300 (sm_103a).
 
 Implements the family of Huang, Smith, Henry and van de Geijn, "Implementing
-Strassen's Algorithm with BLIS" (arXiv:1605.01078): one- and two-level Strassen in the
+Strassen's Algorithm with BLIS" (arXiv:1605.01078): one-, two- and three-level Strassen in the
 ABC, AB and Naive variants plus the classical product, behind the C ABI of
 ``include/strassen.h``.  This package is the thin Python side of that ABI:
 
