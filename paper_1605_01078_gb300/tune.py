@@ -303,6 +303,10 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--out", required=True)
     ap.add_argument("--sweep", action="store_true", help="run the FP64 shape sweep only")
+    ap.add_argument("--train-rows", default=None,
+                    help="train on timed rows saved by an earlier run (JSON) instead of timing training shapes")
+    ap.add_argument("--heldout-seed", type=int, default=2)
+    ap.add_argument("--oz-heldout-seed", type=int, default=4)
     ap.add_argument("--evaluate", default=None,
                     help="a selector JSON (as shipped in data/): measure only the held-out shapes and report "
                          "the regret of that network, the analytic model and the fixed rules")
@@ -322,8 +326,8 @@ def main(argv=None) -> int:
     if a.evaluate:
         with open(a.evaluate) as fh:
             params = np.array(json.load(fh)["params"], dtype=np.float32)
-        held_rows = measure(W.loguniform_shapes(a.heldout, 2, a.lo, a.hi), f64, timer)
-        held_oz = measure(W.loguniform_shapes(a.oz_heldout, 4, a.lo, a.hi), oz, timer)
+        held_rows = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, timer)
+        held_oz = measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, timer)
         summary = {"shapes_heldout_f64": len(held_rows), "shapes_heldout_oz": len(held_oz),
                    "seconds_measuring": time.time() - t0}
         for name, rows in (("f64", held_rows), ("oz_bf16", held_oz)):
@@ -341,11 +345,14 @@ def main(argv=None) -> int:
             json.dump(summary, fh, indent=1)
         print(json.dumps({k: summary[k] for k in ("f64", "oz_bf16")}, indent=1))
         return 0
-    train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, timer)
-    train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, timer)
+    if a.train_rows:
+        train_rows = load_rows(a.train_rows)
+    else:
+        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, timer)
+        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, timer)
     t_train = time.time() - t0
-    held_rows = measure(W.loguniform_shapes(a.heldout, 2, a.lo, a.hi), f64, timer)
-    held_oz = measure(W.loguniform_shapes(a.oz_heldout, 4, a.lo, a.hi), oz, timer)
+    held_rows = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, timer)
+    held_oz = measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, timer)
     t_held = time.time() - t0 - t_train
     params, hist = train(train_rows, steps=a.steps, lr=3e-3, seed=0)
     summary = {"timings_train": int(sum(np.isfinite(r["times"]).sum() for r in train_rows)),
