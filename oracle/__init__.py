@@ -6,9 +6,10 @@ CUDA library in ``paper_1605_01078_gb300`` and never imports it.
 
 Contents
 --------
-* :func:`gemm`, :func:`strassen`, :func:`gemm_sampled` -- thin numpy wrappers over
-  the plain C in ``oracle.c`` (classical definition, Section 2.1; recursive textbook
-  Strassen per Figure 1, Sections 3.1-3.3; Dot2-compensated sampled entries).
+* :func:`gemm`, :func:`strassen`, :func:`strassen_sampled`, :func:`gemm_sampled` --
+  thin numpy wrappers over the plain C in ``oracle.c`` (classical definition, Section
+  2.1; recursive textbook Strassen per Figure 1, Sections 3.1-3.3, in full or entry by
+  entry; Dot2-compensated sampled entries).
 * :func:`dgemm` -- alpha op(A) op(B) + beta C by that definition (Section 2.2).
 * :mod:`oracle.tables` -- the one-level table of Figure 1 and the L-level tables of
   Eq. 4 built as Kronecker powers of it (Sections 3.5-3.6).
@@ -54,6 +55,9 @@ def _load():
         lib.oracle_gemm.argtypes = [i64, i64, i64, dp, i64, dp, i64, dp, i64]
         lib.oracle_strassen.restype = i64
         lib.oracle_strassen.argtypes = [ctypes.c_int, i64, i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.oracle_strassen_sampled.restype = ctypes.c_int
+        lib.oracle_strassen_sampled.argtypes = [ctypes.c_int, i64, i64, i64, dp, i64, dp, i64, dp, i64,
+                                                ctypes.POINTER(i64), ctypes.POINTER(i64), i64, dp]
         lib.oracle_gemm_sampled.restype = None
         lib.oracle_gemm_sampled.argtypes = [i64, dp, i64, dp, i64, dp, i64,
                                             ctypes.POINTER(i64), ctypes.POINTER(i64), i64, dp]
@@ -147,6 +151,39 @@ def gemm_sampled(A: np.ndarray, B: np.ndarray, C0: np.ndarray | None,
     return out
 
 
+def strassen_sampled(A: np.ndarray, B: np.ndarray, C0: np.ndarray | None, rows: np.ndarray,
+                     cols: np.ndarray, levels: int) -> np.ndarray:
+    """Entries (rows[t], cols[t]) of the result :func:`strassen` would leave in a copy
+    of C0 (zeros when None), computed one entry at a time in exactly its order of
+    operations (bit for bit the same values), for products too large for the full
+    recursion on a CPU."""
+    _check2d(A, "A"); _check2d(B, "B")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k:
+        raise ValueError("shape mismatch")
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    if rows.shape != cols.shape or rows.ndim != 1:
+        raise ValueError("rows/cols must be 1-D of equal length")
+    if rows.size and (rows.min() < 0 or rows.max() >= m or cols.min() < 0 or cols.max() >= n):
+        raise IndexError("sample index out of range")
+    Bt = np.ascontiguousarray(B.T)
+    out = np.empty(rows.size, dtype=np.float64)
+    if C0 is not None:
+        _check2d(C0, "C0")
+        c0p, ldc = _dp(C0), C0.strides[0] // 8
+    else:
+        c0p, ldc = ctypes.cast(None, ctypes.POINTER(ctypes.c_double)), 0
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    r = _load().oracle_strassen_sampled(int(levels), m, n, k, _dp(A), A.strides[0] // 8, _dp(Bt), k,
+                                        c0p, ldc, rows.ctypes.data_as(P64), cols.ctypes.data_as(P64),
+                                        rows.size, _dp(out))
+    if r < 0:
+        raise MemoryError("oracle_strassen_sampled")
+    return out
+
+
 def max_rel_err(C: np.ndarray, C_ref: np.ndarray, A: np.ndarray, B: np.ndarray) -> float:
     """Element-wise max-norm error scaled by the operands: max|C - C_ref| /
     (max|A| * max|B|).  Zero operands give the plain max error."""
@@ -155,4 +192,4 @@ def max_rel_err(C: np.ndarray, C_ref: np.ndarray, A: np.ndarray, B: np.ndarray) 
     return err / den if den > 0 else err
 
 
-__all__ = ["build", "gemm", "strassen", "gemm_sampled", "max_rel_err"]
+__all__ = ["build", "gemm", "strassen", "strassen_sampled", "gemm_sampled", "max_rel_err"]

@@ -14,6 +14,9 @@
  *                          (Section 3.1), applied recursively (Section 3.2), with
  *                          explicit temporaries and zero padding of odd sizes
  *                          (Section 3.3), and the classical definition at the leaves.
+ *   oracle_strassen_sampled - selected entries of oracle_strassen's result, computed
+ *                          one by one in exactly its order of operations (for
+ *                          products too large for the full recursion on a CPU).
  *   oracle_gemm_sampled  - selected entries of C0 + A*B computed with the compensated
  *                          dot product Dot2 of Ogita, Rump and Oishi, "Accurate sum and
  *                          dot product", SIAM J. Sci. Comput. 26(6), 2005 (Algorithm
@@ -233,4 +236,125 @@ void oracle_gemm_sampled(int64_t k, const double* A, int64_t lda,
     }
     out[t] = s + c;
   }
+}
+
+/* ---------------------------------------------------------------- sampled Strassen */
+
+/* Figure 1 once more, as data, for the entry-by-entry recursion below: for each product
+ * M0..M6 its A terms, its B terms (block row, block column, sign; the first term's sign
+ * is always +) and its C targets.  The rows and term orders are those of the
+ * statements in oracle_strassen, so that every operand sum is formed the same way. */
+typedef struct { int n; int bi[2], bj[2]; double sg[2]; } fig1_terms;
+static const fig1_terms kFig1A[7] = {
+  {2, {0, 1}, {0, 1}, {+1, +1}}, {2, {1, 1}, {0, 1}, {+1, +1}}, {1, {0, 0}, {0, 0}, {+1, 0}},
+  {1, {1, 0}, {1, 0}, {+1, 0}},  {2, {0, 0}, {0, 1}, {+1, +1}}, {2, {1, 0}, {0, 0}, {+1, -1}},
+  {2, {0, 1}, {1, 1}, {+1, -1}}};
+static const fig1_terms kFig1B[7] = {
+  {2, {0, 1}, {0, 1}, {+1, +1}}, {1, {0, 0}, {0, 0}, {+1, 0}},  {2, {0, 1}, {1, 1}, {+1, -1}},
+  {2, {1, 0}, {0, 0}, {+1, -1}}, {1, {1, 0}, {1, 0}, {+1, 0}},  {2, {0, 0}, {0, 1}, {+1, +1}},
+  {2, {1, 1}, {0, 1}, {+1, +1}}};
+static const fig1_terms kFig1C[7] = {
+  {2, {0, 1}, {0, 1}, {+1, +1}}, {2, {1, 1}, {0, 1}, {+1, -1}}, {2, {0, 1}, {1, 1}, {+1, +1}},
+  {2, {0, 1}, {0, 0}, {+1, +1}}, {2, {0, 0}, {1, 0}, {+1, -1}}, {1, {1, 0}, {1, 0}, {+1, 0}},
+  {1, {0, 0}, {0, 0}, {+1, 0}}};
+
+/* A matrix that exists only as a recipe: either stored (element (r, c) at
+ * X[r * rs + c * cs]) or the signed sum of quadrants of a parent, each quadrant
+ * zero-padded past the parent's edge exactly as quad_load pads it. */
+typedef struct vmat {
+  const struct vmat* parent;
+  int64_t rows, cols;
+  const double* X; int64_t rs, cs;          /* stored */
+  int n; int qi[2], qj[2]; double sg[2];   /* sum of parent quadrants */
+} vmat;
+
+/* out[0..cols) = row r of v (r < v->rows); returns 0, or -1 if out of memory. */
+static int vmat_row(const vmat* v, int64_t r, double* out) {
+  if (!v->parent) {
+    for (int64_t c = 0; c < v->cols; ++c) out[c] = v->X[r * v->rs + c * v->cs];
+    return 0;
+  }
+  const vmat* p = v->parent;
+  double* buf = (double*)malloc(sizeof(double) * (size_t)(p->cols > 0 ? p->cols : 1));
+  if (!buf) return -1;
+  for (int t = 0; t < v->n; ++t) {
+    const int64_t pr = v->qi[t] * v->rows + r;  /* the parent's row of this quadrant row */
+    if (pr < p->rows) {
+      if (vmat_row(p, pr, buf) < 0) { free(buf); return -1; }
+    }
+    for (int64_t c = 0; c < v->cols; ++c) {
+      const int64_t pc = v->qj[t] * v->cols + c;
+      const double x = (pr < p->rows && pc < p->cols) ? buf[pc] : 0.0;
+      /* blk_copy for the first term, blk_add's x + s*y for the second */
+      out[c] = (t == 0) ? x : out[c] + v->sg[t] * x;
+    }
+  }
+  free(buf);
+  return 0;
+}
+
+/* Entry (i, j) of c0 + (levels-level textbook Strassen of a (m x k) and bt^T, where bt
+ * holds B transposed (n x k)), with the operations of oracle_strassen in its order:
+ * per product the operand sums, the product recursively into a zeroed M, then
+ * C += sign * M for the product's target quadrant; at the leaves the classical sum
+ * over p in ascending order, then one addition into the target.  Returns 0 or -1. */
+static int strassen_entry(int levels, const vmat* a, const vmat* bt, int64_t i, int64_t j, double c0,
+                          double* out) {
+  const int64_t m = a->rows, n = bt->rows, k = a->cols;
+  if (levels <= 0) {
+    double* ra = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    double* rb = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    if (!ra || !rb || vmat_row(a, i, ra) < 0 || vmat_row(bt, j, rb) < 0) { free(ra); free(rb); return -1; }
+    double s = 0.0;
+    for (int64_t p = 0; p < k; ++p) s += ra[p] * rb[p];
+    free(ra); free(rb);
+    *out = c0 + s;
+    return 0;
+  }
+  const int64_t hm = (m + 1) / 2, hn = (n + 1) / 2, hk = (k + 1) / 2;
+  const int qi = (int)(i / hm), qj = (int)(j / hn);
+  const int64_t li = i - qi * hm, lj = j - qj * hn;
+  double c = c0;
+  for (int r = 0; r < 7; ++r) {
+    double g = 0.0;
+    for (int t = 0; t < kFig1C[r].n; ++t)
+      if (kFig1C[r].bi[t] == qi && kFig1C[r].bj[t] == qj) g = kFig1C[r].sg[t];
+    if (g == 0.0) continue;
+    vmat sa, sb;
+    memset(&sa, 0, sizeof(sa)); memset(&sb, 0, sizeof(sb));
+    sa.parent = a; sa.rows = hm; sa.cols = hk; sa.n = kFig1A[r].n;
+    sb.parent = bt; sb.rows = hn; sb.cols = hk; sb.n = kFig1B[r].n;
+    for (int t = 0; t < 2; ++t) {
+      sa.qi[t] = kFig1A[r].bi[t]; sa.qj[t] = kFig1A[r].bj[t]; sa.sg[t] = kFig1A[r].sg[t];
+      /* quadrant (bi, bj) of B is quadrant (bj, bi) of its transpose */
+      sb.qi[t] = kFig1B[r].bj[t]; sb.qj[t] = kFig1B[r].bi[t]; sb.sg[t] = kFig1B[r].sg[t];
+    }
+    double M;
+    if (strassen_entry(levels - 1, &sa, &sb, li, lj, 0.0, &M) < 0) return -1;
+    c += g * M;
+  }
+  *out = c;
+  return 0;
+}
+
+/* For t = 0..count-1: out[t] = entry (rows[t], cols[t]) of what oracle_strassen(levels,
+ * m, n, k, A, lda, B, ldb, C) leaves in C when C starts as C0 (NULL: zeros), bit for
+ * bit.  B is passed transposed: Bt is n x k with row stride ldbt.  Returns 0 or -1. */
+int oracle_strassen_sampled(int levels, int64_t m, int64_t n, int64_t k,
+                            const double* A, int64_t lda,
+                            const double* Bt, int64_t ldbt,
+                            const double* C0, int64_t ldc,
+                            const int64_t* rows, const int64_t* cols, int64_t count,
+                            double* out) {
+  vmat a, bt;
+  memset(&a, 0, sizeof(a)); memset(&bt, 0, sizeof(bt));
+  a.rows = m; a.cols = k; a.X = A; a.rs = lda; a.cs = 1;
+  bt.rows = n; bt.cols = k; bt.X = Bt; bt.rs = ldbt; bt.cs = 1;
+  for (int64_t t = 0; t < count; ++t) {
+    const int64_t i = rows[t], j = cols[t];
+    const double c0 = C0 ? C0[i * ldc + j] : 0.0;
+    if (k <= 0) { out[t] = c0; continue; }
+    if (strassen_entry(levels, &a, &bt, i, j, c0, &out[t]) < 0) return -1;
+  }
+  return 0;
 }

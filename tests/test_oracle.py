@@ -181,6 +181,31 @@ def test_three_level_table_is_the_associative_kronecker_cube():
     assert c3["products"] == 343 and c3["a_terms"] == 12 ** 3 and c3["c_updates"] == 12 ** 3
 
 
+@pytest.mark.parametrize("levels", [0, 1, 2, 3])
+@pytest.mark.parametrize("m,n,k", [(37, 41, 29), (1, 9, 4), (64, 64, 64), (100, 77, 130)])
+def test_strassen_sampled_equals_full_recursion(levels, m, n, k):
+    """The entry-by-entry textbook Strassen repeats the full recursion's operations in
+    its order: on float inputs (where every rounding shows) and ragged shapes (padding
+    at every level) every entry agrees bit for bit, with and without C0."""
+    A, B, C = W.uniform(m, k, 1), W.uniform(k, n, 2), W.uniform(m, n, 3)
+    rows, cols = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    for C0 in (C, None):
+        full = np.zeros((m, n)) if C0 is None else C0.copy()
+        oracle.strassen(A, B, full, levels)
+        got = oracle.strassen_sampled(A, B, C0, rows.ravel(), cols.ravel(), levels).reshape(m, n)
+        assert np.array_equal(got, full)
+
+
+def test_strassen_sampled_exact_on_integers_and_strided_operands():
+    A = W.integer(23, 19, 4, ld=25)
+    B = W.integer(19, 17, 5, ld=20)
+    C = W.integer(23, 17, 6)
+    ref = brute(np.ascontiguousarray(A), np.ascontiguousarray(B), C)
+    rows, cols = W.sample_indices(23, 17, 50, 3)
+    for L in (1, 2, 3):
+        assert np.array_equal(oracle.strassen_sampled(A, B, C, rows, cols, L), ref[rows, cols])
+
+
 @pytest.mark.parametrize("levels,tol", [(1, 1e-13), (2, 1e-12), (3, 1e-12)])
 def test_strassen_float_error_scale(levels, tol):
     n = 192
