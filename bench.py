@@ -1,24 +1,29 @@
 #!/usr/bin/env python
 """Benchmark of the Strassen-fused FP64 GEMM on GB300 (one JSON line on rank 0).
 
-Workload (default): m = n = k = 8192, FP64, A, B, C i.i.d. uniform[-1, 1] from fixed
-seeds, C += A*B (accumulate mode), 2-level ABC Strassen.  One step = one
-strassen_gemm call through the C ABI on inputs resident in HBM (1.5 GB of operands,
-larger than the 129 MB L2, so no flush is needed between steps).
+Workload (default): m = n = k = 16384, FP64, A, B, C i.i.d. uniform[-1, 1] from fixed
+seeds, C += A*B (accumulate mode), 2-level ABC Strassen -- the largest square size of
+the FP64 shape sweep.  One step = one strassen_gemm call through the C ABI on inputs
+resident in HBM (6 GB of operands, larger than the 129 MB L2, so no flush is needed
+between steps).
 
-Metric: effective GFLOPS = 2mnk / t * 1e-9 (the paper's Eq. for effective GFLOPS).
-Also reported: the library's classical FP64 kernel on the same inputs (the
-comparator), the same product with one and three levels, an end-to-end figure with
-host buffers, the roofline of the FP64 product
-kernel against the FP64 pipe, SM clocks sampled during the timed region, and the CPU
-oracle timed on a bounded sample.
+Metric: effective GFLOPS = 2mnk / t * 1e-9 (the paper's effective GFLOPS of Section 5).
+Also reported: the library's classical FP64 kernel on the same inputs (the comparator),
+the same call with STRASSEN_FLAG_DETERMINISTIC (owner schedule), the strict max-norm
+error max|C - C_exact| / (max|A| max|B|) and the Frobenius error of one call on sampled
+entries next to the textbook Strassen's (the CPU leg computes the exact entries with
+Dot2 and the textbook ones with the oracle), the one- and three-level products at
+8192^3, an end-to-end figure with host buffers, the roofline of the FP64 product kernel
+against the FP64 pipe, SM clocks sampled during the timed region, the batched and
+split-precision workloads, and the CPU oracle timed on all host cores and on one.
 
 Multi-GPU: the path does not shard into a collective; N ranks run N independent
 replicas ("replicas only"), value = total effective flops of all ranks / the slowest
 rank's time.
 
---impl reference times the CPU oracle (textbook recursive Strassen, plain C, one
-thread) on a bounded sample of the same workload (m = n = k = 1024 per step).
+--impl reference times the CPU oracle (textbook recursive Strassen, plain C, OpenMP
+timing build on all host cores) on a bounded sample of the workload (m = n = k = 4096
+per step).
 """
 from __future__ import annotations
 
@@ -39,8 +44,10 @@ METRIC = "effective GFLOPS (2mnk/t) Strassen vs classical GEMM, 1 GB300, rel err
 UNIT = "GFLOP/s"
 # FP64 pipe peak: 2 FMA lanes (4 flops) per clock per SM x 152 SMs x 2070 MHz max clock.
 FP64_PEAK_GFLOPS = 4 * 152 * 2070e6 / 1e9
-CPU_SAMPLE_N = 2048
-REF_SAMPLE_N = 1024
+CPU_SAMPLE_N = 4096       # all host cores
+CPU_SAMPLE_N_1CORE = 2048
+REF_SAMPLE_N = 4096
+ERR_SAMPLES = 4096        # sampled entries for the error figures
 
 
 def parse():
@@ -49,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--levels", type=int, default=2)
     ap.add_argument("--variant", default="ABC")
     ap.add_argument("--dtype", default="f64", choices=["f64", "oz_bf16"])
@@ -58,6 +65,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-levels", action="store_true", help="skip the other level counts (1 and 3 levels)")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the sampled error figures")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="only time the CPU oracle (1 core and all cores, n = 1024..8192) and print the table")
     return ap.parse_args()
 
 
@@ -140,7 +150,7 @@ class ClockSampler:
 
 # The sources the FP64 product kernel is compiled from (its recorded traffic is valid
 # only while they are unchanged).
-KERNEL_SOURCES = ("fp64_gemm.cu", "int_fadd.h", "plan_tables.h")
+KERNEL_SOURCES = ("fp64_gemm.cu", "int_fadd.h", "plan_tables.h", "internal.h")
 
 
 def kernel_source_sha256():
@@ -150,9 +160,9 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the FP64 product kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def recorded_traffic(n, levels, variant):
+    """DRAM bytes per launch of the FP64 product kernel for this workload from the
+    committed ncu summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "fp64_strassen_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -164,16 +174,108 @@ def recorded_traffic():
     if rec.get("kernel_source_sha256") != kernel_source_sha256():
         return None
     try:
-        return float(rec["dram_bytes_per_launch_8192_2L_ABC"])
+        return float(rec[f"dram_bytes_per_launch_{n}_{levels}L_{variant.upper()}"])
     except (KeyError, ValueError):
         return None
 
 
+def timed_calls(torch, fn, reps, stream):
+    """Median seconds of `reps` calls of fn() (CUDA events on the launching stream),
+    after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) / 1e3 for a, b in ev)
+
+
+# ---------------------------------------------------------------- CPU leg (oracle)
+
+def cpu_leg_errors(A, B, C0, got, rows, cols, levels):
+    """The CPU leg's accuracy figures for one GPU call C = C0 + A B whose entries
+    (rows, cols) are `got`: the exact entries (Dot2, rounded once) and the textbook
+    recursive Strassen's entries (the oracle, entry by entry) on the same samples.
+    strict = max|C - C_exact| / (max|A| max|B|); frobenius = ||C - C_exact||_F /
+    (||A||_F ||B||_F), its numerator estimated from the samples."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    exact = oracle.gemm_sampled(A, B, C0, rows, cols)
+    den = float(np.max(np.abs(A))) * float(np.max(np.abs(B)))
+    m, n = C0.shape
+    fro_den = float(np.linalg.norm(A)) * float(np.linalg.norm(B))
+
+    def figures(vals):
+        e = np.abs(vals - exact)
+        return float(np.max(e)) / den, float(np.sqrt(m * n * np.mean(e * e))) / fro_den
+
+    strict, fro = figures(got)
+    out = {"strict": strict, "frobenius": fro, "samples": int(rows.size),
+           "tolerance": 1e-13 if levels <= 1 else 1e-12}
+    if levels > 0:
+        tb = oracle.strassen_sampled(A, B, C0, rows, cols, levels)
+        out["textbook_strict"], out["textbook_frobenius"] = figures(tb)
+    return out
+
+
+def cpu_oracle_effective(n, levels, threads, reps=1):
+    """Effective GFLOP/s of the oracle's textbook Strassen (OpenMP timing build) at n^3
+    on `threads` host threads, best of `reps`."""
+    import oracle
+    import workloads as W
+    A, B, C = W.uniform(n, n, 0), W.uniform(n, n, 1), W.uniform(n, n, 2)
+    oracle.build_timing()
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.strassen_timed(A, B, C, levels, threads)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return 2.0 * n ** 3 / best / 1e9, best
+
+
+def cpu_baseline(levels):
+    """The oracle on all host cores (4096^3) and on one core (2048^3)."""
+    import oracle
+    cores = oracle.host_cores()
+    v, t = cpu_oracle_effective(CPU_SAMPLE_N, levels, cores)
+    v1, t1 = cpu_oracle_effective(CPU_SAMPLE_N_1CORE, levels, 1)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"m=n=k={CPU_SAMPLE_N} {levels}-level textbook Strassen (plain C, -O3, OpenMP over the rows "
+                      f"of each classical leaf product) on {cores} host cores, {t:.1f} s",
+            "one_core": {"value": v1, "unit": UNIT, "cores": 1,
+                         "sample": f"m=n=k={CPU_SAMPLE_N_1CORE} {levels}-level textbook Strassen, 1 thread, "
+                                   f"{t1:.1f} s"}}
+
+
+def cpu_sweep():
+    """1 core and all cores up to 4096, all cores at 8192: one line per row."""
+    import oracle
+    cores = oracle.host_cores()
+    rows = []
+    for n in (1024, 2048, 4096, 8192):
+        for L in (0, 1, 2):
+            for th in ((1, cores) if n <= 4096 else (cores,)):
+                if th == 1 and n == 4096 and L == 0:
+                    continue  # about a minute on one core; the 2-level row covers the size
+                v, t = cpu_oracle_effective(n, L, th)
+                row = {"n": n, "levels": L, "threads": th, "gflops": v, "seconds": t}
+                print(json.dumps(row), flush=True)
+                rows.append(row)
+    return rows
+
+
+# ---------------------------------------------------------------- GPU side sections
+
 def bench_batched(sg, W, torch, reps=3):
     """256 FP64 problems, m, n, k log-uniform in [256, 4096] (seed 0), levels and block
-    tiles chosen by the library, in one batched call (one persistent launch per tile)
-    captured in a CUDA graph; against a loop of 256 classical launches on the same
-    operands."""
+    tiles chosen by the library, in one batched call captured in a CUDA graph; against
+    a loop of 256 classical launches and a loop of 256 automatic single calls on the
+    same operands."""
     shapes = W.loguniform_shapes(256, seed=0, lo=256, hi=4096)
     mats = [(W.uniform_device(m, k, 1000 + i), W.uniform_device(k, n, 2000 + i), W.uniform_device(m, n, 3000 + i))
             for i, (m, n, k) in enumerate(shapes)]
@@ -183,158 +285,149 @@ def bench_batched(sg, W, torch, reps=3):
                                      A.stride(0), B.stride(0), C.stride(0), -1, sg.STRASSEN_AUTO)
     flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
     stream = torch.cuda.current_stream()
-    assert sg.strassen_gemm_batched(len(mats), arr, 0, stream.cuda_stream) == 0
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        assert sg.strassen_gemm_batched(len(mats), arr, 0, torch.cuda.current_stream().cuda_stream) == 0
-    g.replay()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
+
+    def graph_of(problems):
+        assert sg.strassen_gemm_batched(len(mats), problems, 0, stream.cuda_stream) == 0
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            assert sg.strassen_gemm_batched(len(mats), problems, 0, torch.cuda.current_stream().cuda_stream) == 0
         g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    t_graph = e0.elapsed_time(e1) / 1e3 / reps
-    for A, B, C in mats:
-        sg.classical(A, B, C)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        for A, B, C in mats:
-            sg.classical(A, B, C)
-    e1.record()
-    torch.cuda.synchronize()
-    t_loop = e0.elapsed_time(e1) / 1e3 / reps
+        torch.cuda.synchronize()
+        return g
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    g = graph_of(arr)
+    t_graph = timed(g.replay)
+    t_loop = timed(lambda: [sg.classical(A, B, C) for A, B, C in mats])
+    t_auto = timed(lambda: [sg.gemm(A, B, C, levels=-1, variant="AUTO") for A, B, C in mats])
     # the same batched call with every problem classical: isolates the launch from the level choice
     for i in range(len(mats)):
         arr[i].levels = 0
         arr[i].variant = sg.STRASSEN_ABC
-    g0 = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g0):
-        assert sg.strassen_gemm_batched(len(mats), arr, 0, torch.cuda.current_stream().cuda_stream) == 0
-    g0.replay()
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        g0.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    t_graph0 = e0.elapsed_time(e1) / 1e3 / reps
-    return {"workload": "256 FP64 problems, m,n,k log-uniform in [256,4096] (seed 0), one batched call (one persistent "
-                        "launch per block tile) in a CUDA graph",
+    g0 = graph_of(arr)
+    t_graph0 = timed(g0.replay)
+    return {"workload": "256 FP64 problems, m,n,k log-uniform in [256,4096] (seed 0), one batched call in a CUDA "
+                        "graph, levels and tiles chosen by the library",
             "value": flops / t_graph / 1e9, "unit": UNIT, "ms": t_graph * 1e3,
             "all_classical_batched": {"value": flops / t_graph0 / 1e9, "ms": t_graph0 * 1e3},
             "loop_of_classical": {"value": flops / t_loop / 1e9, "ms": t_loop * 1e3, "launches": len(mats)},
+            "loop_of_auto_calls": {"value": flops / t_auto / 1e9, "ms": t_auto * 1e3, "calls": len(mats)},
             "speedup_vs_loop": t_loop / t_graph}
 
 
-def bench_split_precision(sg, W, torch, n=8192, err_n=4096, reps=3):
+def split_tensor_flops(m, n, k, L):
+    """Tensor-core work of the slice products: 28 digit pairs x 2 h_mp h_np h_kp x 7^L
+    (padded block edges: 128 rows of A, 256 columns of B, 64 of k)."""
+    P = 1 << L
+
+    def padded(d, q):
+        h = -(-d // P)
+        return -(-h // q) * q
+
+    return 28 * 2.0 * padded(m, 128) * padded(n, 256) * padded(k, 64) * 7 ** L
+
+
+def bench_split_precision(sg, W, torch, sizes=(8192, 16384), err_n=8192, reps=3, with_errors=True):
     """Split-precision FP64 emulation (BF16 digit slices on the tensor cores): effective
-    GFLOP/s at n^3 for 0, 1, 2 levels and at (2n)^3 for level 0, and the max-norm error
-    against the library's
-    plain FP64 classical result (normwise: / (||A||_inf max|B|)) for inputs
-    u * 2^round(N(0, sigma)) at err_n^3."""
-    out = {"workload": f"m=n=k={n} FP64 via BF16 slices, A,B,C uniform[-1,1]", "levels": {}}
-    A, B, C = W.uniform_device(n, n, 11), W.uniform_device(n, n, 12), W.uniform_device(n, n, 13)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for L in (0, 1, 2):
-        sg.gemm(A, B, C, levels=L, dtype="oz_bf16")
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            sg.gemm(A, B, C, levels=L, dtype="oz_bf16")
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3 / reps
-        out["levels"][str(L)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3}
-    del A, B, C
-    # the larger square size of the split-precision workload, classical slices
-    n2 = 2 * n
-    A, B, C = W.uniform_device(n2, n2, 14), W.uniform_device(n2, n2, 15), W.uniform_device(n2, n2, 16)
-    sg.gemm(A, B, C, levels=0, dtype="oz_bf16")
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(reps):
-        sg.gemm(A, B, C, levels=0, dtype="oz_bf16")
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / reps
-    out[f"n{n2}_level0"] = {"value": 2.0 * n2 ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3}
-    del A, B, C
-    errs = {}
-    for sigma in (0, 4, 10):
-        A = torch.from_numpy(W.scaled(err_n, err_n, 21, sigma)).cuda()
-        B = torch.from_numpy(W.scaled(err_n, err_n, 22, sigma)).cuda()
-        ref = torch.zeros((err_n, err_n), dtype=torch.float64, device="cuda")
-        sg.classical(A, B, ref)
-        den = float(torch.max(torch.sum(torch.abs(A), dim=1))) * float(torch.max(torch.abs(B)))
+    GFLOP/s for 0, 1, 2 levels at each size, the per-stage times of one call
+    (strassen_profile_split_precision) with the slice-product kernel's tensor-pipe
+    fraction of the measured BF16 peak, and the errors against the exact product
+    (Dot2-sampled, the CPU leg) for inputs u * 2^round(N(0, sigma)) at err_n^3."""
+    import numpy as np
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    out = {"workload": "m=n=k in {8192, 16384} FP64 via BF16 digit slices, A,B,C uniform[-1,1]", "sizes": {}}
+    stream = torch.cuda.current_stream()
+    for n in sizes:
+        A, B, C = W.uniform_device(n, n, 11), W.uniform_device(n, n, 12), W.uniform_device(n, n, 13)
         row = {}
         for L in (0, 1, 2):
-            Cz = torch.zeros_like(ref)
-            sg.gemm(A, B, Cz, levels=L, dtype="oz_bf16")
-            torch.cuda.synchronize()
-            row[str(L)] = float(torch.max(torch.abs(Cz - ref))) / den
-        errs[str(sigma)] = row
-    out["error_vs_fp64_classical"] = {"n": err_n, "by_sigma_then_levels": errs}
+            t = timed_calls(torch, lambda: sg.gemm(A, B, C, levels=L, dtype="oz_bf16", stream=stream), reps, stream)
+            ms = sg.strassen_profile_split_precision(n, n, n, A.data_ptr(), n, B.data_ptr(), n, C.data_ptr(), n, L,
+                                                     stream.cuda_stream)
+            tf = split_tensor_flops(n, n, n, L) / (ms[1] / 1e3) / 1e12
+            row[str(L)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3,
+                           "stage_ms": {"splits": ms[0], "slice_products": ms[1], "recombine_scatter": ms[2]},
+                           "oz_gemm_roofline": {"bound": "tensor", "achieved": tf, "peak": bf16, "unit": "TFLOP/s",
+                                                "frac": tf / bf16,
+                                                "peak_note": "measured BF16 dense peak (burst), MEASURED_PEAKS.json"}}
+        out["sizes"][str(n)] = row
+        del A, B, C
+        torch.cuda.empty_cache()
+    if with_errors:
+        import oracle
+        errs = {}
+        rows, cols = W.sample_indices(err_n, err_n, 2048, 5)
+        ri, ci = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
+        for sigma in (0, 4, 10):
+            Ah, Bh = W.scaled(err_n, err_n, 21, sigma), W.scaled(err_n, err_n, 22, sigma)
+            A, B = torch.from_numpy(Ah).cuda(), torch.from_numpy(Bh).cuda()
+            # CPU leg: the exact entries (Dot2, rounded once)
+            exact = oracle.gemm_sampled(Ah, Bh, None, rows, cols)
+            den = float(np.max(np.abs(Ah))) * float(np.max(np.abs(Bh)))
+            den_norm = float(np.max(np.sum(np.abs(Ah), axis=1))) * float(np.max(np.abs(Bh)))
+            fro_den = float(np.linalg.norm(Ah)) * float(np.linalg.norm(Bh))
+
+            def figures(vals):
+                e = np.abs(vals - exact)
+                return {"strict": float(np.max(e)) / den, "normwise": float(np.max(e)) / den_norm,
+                        "frobenius": float(np.sqrt(err_n * err_n * np.mean(e * e))) / fro_den}
+
+            per = {}
+            for L, dt in ((0, "f64"), (0, "oz_bf16"), (1, "oz_bf16"), (2, "oz_bf16")):
+                Cz = torch.zeros((err_n, err_n), dtype=torch.float64, device="cuda")
+                sg.gemm(A, B, Cz, levels=L, dtype=dt)
+                got = Cz[ri, ci].cpu().numpy()
+                del Cz
+                per["fp64_classical" if dt == "f64" else str(L)] = figures(got)
+            errs[str(sigma)] = per
+            del A, B
+        out["error_vs_exact"] = {"n": err_n, "samples": int(rows.size), "by_sigma_then_levels": errs,
+                                 "norms": "strict: max|C - C_exact| / (max|A| max|B|); normwise: / (||A||_inf max|B|); "
+                                          "frobenius: ||C - C_exact||_F / (||A||_F ||B||_F), numerator from the "
+                                          "samples; C_exact from Dot2 (the CPU leg)"}
     return out
 
 
-def level_error(sg, torch, A, B, C, stream, levels, variant="ABC"):
-    """max|C_L - C_0| / (||A||_inf max|B|) of one call against the library's classical
-    result on the same inputs (the normwise reading of the tolerance)."""
-    ref = C.clone()
-    sg.classical(A, B, ref)
-    got = C.clone()
-    sg.gemm(A, B, got, levels=levels, variant=variant, stream=stream)
-    torch.cuda.synchronize()
-    den = float(A.abs().sum(dim=1).max()) * float(B.abs().max())
-    err = float((got - ref).abs().max()) / den
-    del ref, got
-    return err
-
-
-def bench_other_levels(sg, torch, A, B, C, stream, levels_list, variant="ABC", reps=3):
-    """The same product with other level counts (on the same resident inputs): effective
-    GFLOP/s and the FP64 pipe fraction of each (CUDA events per call), and the max-norm
-    error of one call against the library's classical result on the same C
-    (max|C_L - C_0| / (||A||_inf max|B|))."""
-    m, k = A.shape
-    n = B.shape[1]
+def bench_other_levels(sg, torch, W, n, levels_list, variant="ABC", reps=3, accuracy=True):
+    """The same product at n^3 with other level counts on their own resident inputs
+    (seeds 100-102, uniform[-1, 1], accumulate mode): effective GFLOP/s and FP64-pipe
+    fraction (CUDA events per call), and the sampled strict error of one call next to
+    the textbook Strassen's."""
+    Ah, Bh, Ch = W.uniform(n, n, 100), W.uniform(n, n, 101), W.uniform(n, n, 102)
+    A, B, C = torch.from_numpy(Ah).cuda(), torch.from_numpy(Bh).cuda(), torch.from_numpy(Ch).cuda()
+    stream = torch.cuda.current_stream()
+    rows, cols = W.sample_indices(n, n, ERR_SAMPLES // 2, 7)
+    ri, ci = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
     out = {}
     for lv in levels_list:
-        err = level_error(sg, torch, A, B, C, stream, lv, variant)
-        sg.gemm(A, B, C, levels=lv, variant=variant, stream=stream)
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        for a, b in ev:
-            a.record(stream)
-            sg.gemm(A, B, C, levels=lv, variant=variant, stream=stream)
-            b.record(stream)
-        torch.cuda.synchronize()
-        t = statistics.median(a.elapsed_time(b) / 1e3 for a, b in ev)
-        alg = algorithmic_flops(m, n, k, lv) / t / 1e9
-        out[str(lv)] = {"value": 2.0 * m * n * k / t / 1e9, "unit": UNIT, "ms": t * 1e3,
+        err = None
+        if accuracy:
+            C1 = C.clone()
+            sg.gemm(A, B, C1, levels=lv, variant=variant, stream=stream)
+            got = C1[ri, ci].cpu().numpy()
+            del C1
+            err = cpu_leg_errors(Ah, Bh, Ch, got, rows, cols, lv)
+        t = timed_calls(torch, lambda: sg.gemm(A, B, C, levels=lv, variant=variant, stream=stream), reps, stream)
+        alg = algorithmic_flops(n, n, n, lv) / t / 1e9
+        out[str(lv)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3, "n": n,
                         "variant": variant, "algorithmic_gflops": alg, "frac": alg / FP64_PEAK_GFLOPS,
-                        "err_vs_classical": err}
+                        "error": err}
+    del A, B, C
+    torch.cuda.empty_cache()
     return out
-
-
-def cpu_oracle_effective(n, levels, reps=1):
-    import numpy as np
-    import oracle
-    import workloads as W
-    A, B = W.uniform(n, n, 0), W.uniform(n, n, 1)
-    C = W.uniform(n, n, 2)
-    oracle.build()
-    best = None
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        oracle.strassen(A, B, C, levels)
-        dt = time.perf_counter() - t0
-        best = dt if best is None else min(best, dt)
-    return 2.0 * n ** 3 / best / 1e9, best
 
 
 def max_over_ranks(seconds, dist, device):
@@ -361,22 +454,24 @@ def run_reference(args):
     import oracle
     import workloads as W
     n = REF_SAMPLE_N
+    cores = oracle.host_cores()
     A, B, C = W.uniform(n, n, 0), W.uniform(n, n, 1), W.uniform(n, n, 2)
-    oracle.build()
+    oracle.build_timing()
     for _ in range(args.warmup):
-        oracle.strassen(A, B, C, args.levels)
+        oracle.strassen_timed(A, B, C, args.levels, cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.strassen(A, B, C, args.levels)
+        oracle.strassen_timed(A, B, C, args.levels, cores)
     dt = time.perf_counter() - t0
     val = 2.0 * n ** 3 * args.steps / dt / 1e9
-    sample = f"m=n=k={n} {args.levels}-level textbook Strassen per step (oracle, plain C, 1 thread)"
+    sample = (f"m=n=k={n} {args.levels}-level textbook Strassen per step (oracle, plain C, -O3, OpenMP over the rows "
+              f"of each classical leaf product, {cores} host cores)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"square m=n=k={args.n} FP64 {args.levels}-level {args.variant} Strassen, C += A*B"},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
     return 0
@@ -386,6 +481,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_sweep:
+        cpu_sweep()
+        return 0
     import numpy as np
     import torch
 
@@ -407,9 +505,8 @@ def main():
     m = n = k = args.n
     L, variant = args.levels, args.variant
     sg.load_library()
-    A = torch.from_numpy(W.uniform(m, k, 100 + rank)).cuda()
-    B = torch.from_numpy(W.uniform(k, n, 200 + rank)).cuda()
-    C = torch.from_numpy(W.uniform(m, n, 300 + rank)).cuda()
+    Ah, Bh, Ch = W.uniform(m, k, 100 + rank), W.uniform(k, n, 200 + rank), W.uniform(m, n, 300 + rank)
+    A, B, C = torch.from_numpy(Ah).cuda(), torch.from_numpy(Bh).cuda(), torch.from_numpy(Ch).cuda()
     stream = torch.cuda.current_stream()
 
     def step():
@@ -421,6 +518,18 @@ def main():
     elif launches_per_step is None:
         nprod = 7 ** L
         launches_per_step = nprod * (2 if variant.upper() == "AB" else 4)
+
+    # Accuracy of one call from the initial C (sampled entries; the CPU leg computes the
+    # exact and the textbook entries), before the timed steps change C.
+    accuracy = None
+    if not args.no_accuracy and rank == 0:
+        rows, cols = W.sample_indices(m, n, ERR_SAMPLES, 7)
+        ri, ci = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
+        C1 = C.clone()
+        sg.gemm(A, B, C1, levels=L, variant=variant, dtype=args.dtype, stream=stream)
+        got = C1[ri, ci].cpu().numpy()
+        del C1
+        accuracy = {"one_call": got}
 
     for _ in range(args.warmup):
         step()
@@ -445,17 +554,16 @@ def main():
     eff_flops = 2.0 * m * n * k
     value = job_gflops(eff_flops, args.steps, ws, elapsed)
 
-    # Comparator: the library's classical kernel on the same inputs.
-    cls_steps = max(2, args.steps // 3)
-    sg.classical(A, B, C)
-    barrier()
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    for _ in range(cls_steps):
-        sg.classical(A, B, C)
-    c1.record(stream)
-    barrier()
-    cls_val = eff_flops * cls_steps / (c0.elapsed_time(c1) / 1e3) / 1e9
+    # Comparators on the same inputs: the library's classical kernel, and the same call
+    # with STRASSEN_FLAG_DETERMINISTIC (owner schedule: bitwise repeatable).
+    cls_t = timed_calls(torch, lambda: sg.classical(A, B, C, stream=stream), 2, stream)
+    cls_val = eff_flops / cls_t / 1e9
+    det = None
+    if args.dtype == "f64" and L > 0:
+        det_t = timed_calls(torch, lambda: sg.gemm(A, B, C, levels=L, variant=variant, stream=stream,
+                                                   deterministic=True), 2, stream)
+        det = {"value": eff_flops / det_t / 1e9, "unit": UNIT, "ms": det_t * 1e3,
+               "flag": "STRASSEN_FLAG_DETERMINISTIC (owner schedule)"}
 
     # End to end through the public API with pinned host buffers: every step copies its
     # inputs A, B, C host -> device and reads its result C back, pipelined on two copy
@@ -495,7 +603,7 @@ def main():
                     load(i + 1)
                 stream.wait_event(ev_in[b])
                 dA, dB, dC = bufs[b]
-                sg.gemm(dA, dB, dC, levels=L, variant=variant, stream=stream)
+                sg.gemm(dA, dB, dC, levels=L, variant=variant, dtype=args.dtype, stream=stream)
                 ev_comp[b].record(stream)
                 d2h.wait_event(ev_comp[b])
                 with torch.cuda.stream(d2h):
@@ -514,20 +622,21 @@ def main():
         e2e = {"value": job_gflops(eff_flops, e_steps, ws, et), "unit": UNIT,
                "h2d_bytes_per_step": int(3 * 8 * m * n), "d2h_bytes_per_step": int(8 * m * n),
                "steps": e_steps, "pipelined": "inputs of step i+1 copied while step i computes (two buffers)"}
-        del bufs
+        del bufs, hA, hB, hC, hOut
+    del A, B, C
+    torch.cuda.empty_cache()
 
-    err_headline = None
-    if args.dtype == "f64" and rank == 0 and m <= 8192:
-        err_headline = level_error(sg, torch, A, B, C, stream, L, variant)
     levels_other = None
     small = None
     if not args.no_levels and args.dtype == "f64" and rank == 0:
-        levels_other = bench_other_levels(sg, torch, A, B, C, stream, [lv for lv in (1, 2, 3) if lv != L])
+        levels_other = bench_other_levels(sg, torch, W, 8192, [1, 2, 3], accuracy=not args.no_accuracy)
         # the small square case: m = n = k = 1024, one-level ABC, C = 0
         As, Bs = W.uniform_device(1024, 1024, 0), W.uniform_device(1024, 1024, 1)
         Cs = torch.zeros((1024, 1024), dtype=torch.float64, device="cuda")
         small = {"workload": "m=n=k=1024, one-level ABC, C = 0 (uniform[-1,1])"}
-        small.update(bench_other_levels(sg, torch, As, Bs, Cs, stream, [1], reps=20)["1"])
+        t = timed_calls(torch, lambda: sg.gemm(As, Bs, Cs, levels=1, stream=stream), 20, stream)
+        small.update({"value": 2.0 * 1024 ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3,
+                      "frac": algorithmic_flops(1024, 1024, 1024, 1) / t / 1e9 / FP64_PEAK_GFLOPS})
         del As, Bs, Cs
 
     batched = None
@@ -535,26 +644,20 @@ def main():
         batched = bench_batched(sg, W, torch)
     split = None
     if not args.no_split and rank == 0:
-        split = bench_split_precision(sg, W, torch)
+        split = bench_split_precision(sg, W, torch, with_errors=not args.no_accuracy)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
+    if accuracy is not None:
+        accuracy = cpu_leg_errors(Ah, Bh, Ch, accuracy["one_call"], rows, cols, L if args.dtype == "f64" else 0)
     alg = algorithmic_flops(m, n, k, L)
     launch_s = statistics.mean(per_launch)
     achieved = alg / launch_s / 1e9
     if args.dtype == "oz_bf16":
-        # tensor-core work of the slice products: 28 digit pairs x 2 h_m h_n h_k x 7^L
-        P = 1 << L
-
-        def padded(d, q):  # ceil(d / 2^L) rounded up to the tile edge q
-            h = -(-d // P)
-            return -(-h // q) * q
-
-        hmp, hnp, hkp = padded(m, 128), padded(n, 256), padded(k, 64)
-        mma = 28 * 2.0 * hmp * hnp * hkp * 7 ** L / launch_s / 1e12
+        mma = split_tensor_flops(m, n, k, L) / launch_s / 1e12
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
@@ -562,17 +665,15 @@ def main():
                 "traffic": None, "kernel": "whole split-precision call (split, oz_gemm, recombine)",
                 "peak_note": "measured BF16 dense peak (burst); per call, not per kernel"}
     else:
-        roof = None
-    roof = roof or {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS,
-            "traffic": recorded_traffic() if (L == 2 and variant.upper() == "ABC" and m == 8192) else None,
-            "kernel": "fp64_strassen_kernel",
-            "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz (derived); DFMA probe measured 1200 GFLOP/s"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS,
+                "traffic": recorded_traffic(m, L, variant) if m == n == k else None,
+                "algorithmic_bytes": algorithmic_bytes(m, n, k, L),
+                "kernel": "fp64_strassen_kernel",
+                "peak_note": "FP64 pipe: 4 flop/clk/SM x 152 SMs x 2070 MHz (derived); DFMA probe measured 1200 GFLOP/s"}
     cpu = None
     if not args.no_cpu_baseline:
-        cv, ct = cpu_oracle_effective(CPU_SAMPLE_N, L)
-        cpu = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"m=n=k={CPU_SAMPLE_N} {L}-level textbook Strassen (plain C, 1 thread), {ct:.1f} s"}
+        cpu = cpu_baseline(L)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -582,7 +683,8 @@ def main():
                    "m": m, "n": n, "k": k, "levels": L, "variant": variant, "products": args.dtype,
                    "parallelism": f"replicas{ws}", "l2": "inputs larger than L2 (3 x 8 m n bytes)"},
         "classical": {"value": cls_val, "unit": UNIT, "speedup": value / ws / cls_val},
-        "err_vs_classical": err_headline,
+        "deterministic": det,
+        "error": accuracy,
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -597,6 +699,13 @@ def main():
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def algorithmic_bytes(m, n, k, levels):
+    """Minimum HBM bytes of one ABC launch with every operand term read once per product
+    and every C update a read and a write: 3^L (mk + kn) 8 B + 3^L mn 16 B (the table
+    has 12^L terms per operand over 4^L blocks, 3^L blocks' worth per product family)."""
+    return 3 ** levels * (m * k + k * n) * 8.0 + 3 ** levels * m * n * 16.0
 
 
 if __name__ == "__main__":

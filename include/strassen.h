@@ -118,9 +118,13 @@ typedef enum {
  * Returns STRASSEN_OK or a negative status; on error C is untouched unless the status
  * is STRASSEN_ERR_CUDA (work may have been partly launched).  ABC in FP64 with the
  * default scheduling accumulates the partial products into C with device atomics, so
- * the rounding order (not the mathematical result) can vary from run to run; set the
- * environment variable STRASSEN_DETERMINISTIC=1 to make every C tile owned by one
+ * the rounding order (not the mathematical result) can vary from run to run;
+ * strassen_dgemm_ex with STRASSEN_FLAG_DETERMINISTIC makes every C tile owned by one
  * thread block, which fixes the order (at some cost in load balance).
+ *
+ * Accuracy: each FP64 partial product is accumulated over at most 256 of k (128 at
+ * three levels) in registers and then added into C (or M), so no sequential sum is
+ * longer than that chunk plus the number of chunks and products per C element.
  */
 STRASSEN_API int strassen_gemm(int64_t m, int64_t n, int64_t k,
                   const double* A, int64_t lda,
@@ -169,6 +173,29 @@ STRASSEN_API int strassen_dgemm(int transa, int transb, int64_t m, int64_t n, in
                                 const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                                 double* C, int64_t ldc, int levels, strassen_variant variant,
                                 strassen_dtype dtype, strassen_stream_t stream);
+
+/* Flags of strassen_dgemm_ex. */
+#define STRASSEN_FLAG_DETERMINISTIC 1u /* fixed rounding order: bitwise the same result on every run */
+
+/*
+ * strassen_dgemm_ex -- strassen_dgemm with options.  Arguments as strassen_dgemm, plus
+ *
+ *   flags   0 or STRASSEN_FLAG_DETERMINISTIC.  With the flag, every FP64 product
+ *           launch (ABC, the product kernels of AB and Naive, classical) gives each C
+ *           tile (or tile of the temporary M) to one thread block, which adds the
+ *           partial products of every element in one fixed order (products in table
+ *           order, k chunks in ascending order): the same inputs give bitwise the same
+ *           C on every run and every GPU of the same kind.  Without it the library may
+ *           split the k range of a tile over blocks (stream-K) for load balance, and
+ *           the order of the atomic C additions then varies.  The split-precision path
+ *           is deterministic either way.  Other bits: STRASSEN_ERR_ARG.
+ *
+ * strassen_gemm(...) is strassen_dgemm_ex(0, 0, ..., alpha 1, beta 1, ..., flags 0).
+ */
+STRASSEN_API int strassen_dgemm_ex(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha,
+                                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                                   double* C, int64_t ldc, int levels, strassen_variant variant,
+                                   strassen_dtype dtype, unsigned flags, strassen_stream_t stream);
 
 /* One problem of a batched call: C += A*B as in strassen_gemm. */
 typedef struct {
@@ -358,6 +385,19 @@ STRASSEN_API int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stre
  */
 STRASSEN_API int strassen_check_int_fadd(int64_t count, uint64_t seed, uint64_t* mismatches,
                                          strassen_stream_t stream);
+
+/*
+ * strassen_profile_split_precision -- diagnostic: one split-precision product
+ * C += A*B (strassen_gemm with dtype STRASSEN_F64_OZ_BF16, variant ABC, `levels` 0-3;
+ * same arguments, layout and checks) with CUDA events between its three stages, then a
+ * wait for the call.  stage_ms (HOST, 3 floats) receives the milliseconds of
+ * [0] the operand splits (operand sums, scaling, digit extraction: three kernels),
+ * [1] the tensor-core slice products (one kernel), [2] the recombination with the C
+ * scatter (one kernel).  Returns STRASSEN_OK or a negative status.
+ */
+STRASSEN_API int strassen_profile_split_precision(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                                                  const double* B, int64_t ldb, double* C, int64_t ldc,
+                                                  int levels, float* stage_ms, strassen_stream_t stream);
 
 /* strassen_status_string -- a static, NUL-terminated description of a status code. */
 STRASSEN_API const char* strassen_status_string(int status);

@@ -11,6 +11,8 @@ Contents
   2.1; recursive textbook Strassen per Figure 1, Sections 3.1-3.3, in full or entry by
   entry; Dot2-compensated sampled entries).
 * :func:`dgemm` -- alpha op(A) op(B) + beta C by that definition (Section 2.2).
+* :func:`dsyrk` -- the symmetric rank-k update alpha op(A) op(A)^T + beta C on one
+  triangle, by the same definition (a level-3 BLAS user of the method, Section 6).
 * :mod:`oracle.tables` -- the one-level table of Figure 1 and the L-level tables of
   Eq. 4 built as Kronecker powers of it (Sections 3.5-3.6).
 * :mod:`oracle.ozaki` -- error-free splitting of FP64 operands into integer slices
@@ -43,6 +45,57 @@ def build(force: bool = False) -> str:
                                "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
+
+
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
+_omp = None
+
+
+def build_timing(force: bool = False) -> str:
+    """Compile the timing variant ``liboracle_omp.so``: the same source at -O3 with
+    OpenMP (the rows of each classical product split over threads), still without
+    contraction into fma, so every entry is computed exactly as in :func:`build`."""
+    if force or not os.path.exists(_OMP_PATH) or (
+            os.path.getmtime(_OMP_PATH) < os.path.getmtime(_SRC)):
+        tmp = _OMP_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC])
+        os.replace(tmp, _OMP_PATH)
+    return _OMP_PATH
+
+
+def host_cores() -> int:
+    """Cores this process may run on (sched_getaffinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def strassen_timed(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int, threads: int) -> int:
+    """:func:`strassen` from the OpenMP timing build on ``threads`` threads (for timing
+    the oracle on the host's cores; results equal :func:`strassen`'s)."""
+    global _omp
+    _check2d(A, "A"); _check2d(B, "B"); _check2d(C, "C")
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or C.shape != (m, n):
+        raise ValueError("shape mismatch")
+    if _omp is None:
+        build_timing()
+        lib = ctypes.CDLL(_OMP_PATH)
+        i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+        lib.oracle_strassen.restype = i64
+        lib.oracle_strassen.argtypes = [ctypes.c_int, i64, i64, i64, dp, i64, dp, i64, dp, i64]
+        lib.omp_set_num_threads.restype = None
+        lib.omp_set_num_threads.argtypes = [ctypes.c_int]
+        _omp = lib
+    _omp.omp_set_num_threads(int(threads))
+    r = _omp.oracle_strassen(int(levels), m, n, k, _dp(A), A.strides[0] // 8, _dp(B), B.strides[0] // 8,
+                             _dp(C), C.strides[0] // 8)
+    if r < 0:
+        raise MemoryError("oracle_strassen")
+    return int(r)
 
 
 def _load():
@@ -106,6 +159,27 @@ def dgemm(transa: int, transb: int, alpha: float, A: np.ndarray, B: np.ndarray, 
         gemm(Aop, Bop, P)
     base = np.zeros_like(P) if beta == 0 else beta * np.asarray(C, dtype=np.float64)
     return base + alpha * P
+
+
+def dsyrk(uplo: int, trans: int, alpha: float, A: np.ndarray, beta: float, C: np.ndarray) -> np.ndarray:
+    """The BLAS symmetric rank-k update on one triangle (a level-3 BLAS operation the
+    paper's conclusion lists among the users of the same Strassen approach):
+    op(A) = A (n x k) for trans = 0, A^T for trans = 1 (A stored k x n); P = op(A) op(A)^T
+    by the classical definition (:func:`gemm`); then for uplo = 0 every entry with
+    j <= i (lower triangle, diagonal included), for uplo = 1 every entry with j >= i,
+    becomes alpha P_ij + beta C_ij (beta = 0 does not read C), and the rest of C is
+    returned unchanged.  Returns a new array."""
+    Aop = np.ascontiguousarray(A.T if trans else A, dtype=np.float64)
+    n = Aop.shape[0]
+    P = np.zeros((n, n))
+    if Aop.shape[1] > 0:
+        gemm(Aop, np.ascontiguousarray(Aop.T), P)
+    out = np.array(C, dtype=np.float64, copy=True)
+    i, j = np.indices((n, n))
+    tri = (j <= i) if uplo == 0 else (j >= i)
+    base = np.zeros_like(P) if beta == 0 else beta * out
+    out[tri] = (base + alpha * P)[tri]
+    return out
 
 
 def strassen(A: np.ndarray, B: np.ndarray, C: np.ndarray, levels: int) -> int:
@@ -192,4 +266,5 @@ def max_rel_err(C: np.ndarray, C_ref: np.ndarray, A: np.ndarray, B: np.ndarray) 
     return err / den if den > 0 else err
 
 
-__all__ = ["build", "gemm", "strassen", "strassen_sampled", "gemm_sampled", "max_rel_err"]
+__all__ = ["build", "build_timing", "host_cores", "gemm", "dgemm", "dsyrk", "strassen", "strassen_timed", "strassen_sampled",
+           "gemm_sampled", "max_rel_err"]

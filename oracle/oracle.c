@@ -6,7 +6,9 @@
  * benchmark load it.  It shares no code, header or table with the CUDA path.
  *
  * Everything is plain IEEE double arithmetic, row-major, one thread, written to be
- * checked against the paper by eye rather than to be fast:
+ * checked against the paper by eye rather than to be fast (a second build with OpenMP,
+ * used only to time the oracle on all host cores, splits the rows of each classical
+ * product over threads without changing any entry's arithmetic):
  *
  *   oracle_gemm          - the definition of C = alpha*A*B + C with alpha = 1
  *                          (Section 2.1): gamma_ij += sum_p alpha_ip * beta_pj.
@@ -49,6 +51,9 @@ int64_t oracle_gemm(int64_t m, int64_t n, int64_t k,
   if (!Bt) return -1;
   for (int64_t p = 0; p < k; ++p)
     for (int64_t j = 0; j < n; ++j) Bt[j * k + p] = B[p * ldb + j];
+  /* Rows of C are independent; the timing build (OpenMP) splits them over threads,
+   * the correctness build ignores this line.  Each entry's arithmetic is the same. */
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m; ++i) {
     const double* a = A + i * lda;
     for (int64_t j = 0; j < n; ++j) {

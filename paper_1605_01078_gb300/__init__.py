@@ -15,16 +15,17 @@ from __future__ import annotations
 
 from . import _binding
 from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  # noqa: F401
-                       STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_NAIVE, StrassenError,
+                       STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_FLAG_DETERMINISTIC, STRASSEN_NAIVE,
+                       StrassenError,
                        classical_gemm, strassen_gemm, strassen_gemm_ab_noalloc, strassen_gemm_batched,
-                       strassen_dgemm,
+                       strassen_dgemm, strassen_dgemm_ex,
                        strassen_plan_table,
                        strassen_problem, strassen_select, strassen_status_string, strassen_device_status,
                        strassen_check_wait_timeout, strassen_tune_record, strassen_tune_clear,
                        strassen_model_seconds, strassen_mlp_param_count, strassen_mlp_forward,
                        strassen_mlp_loss_grad, strassen_mlp_adam, strassen_selector_load,
                        strassen_selector_clear, strassen_check_int_fadd, strassen_selector_use,
-                       strassen_workspace_size)
+                       strassen_workspace_size, strassen_profile_split_precision)
 
 VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO}
 DTYPES = {"f64": STRASSEN_F64, "oz_int8": STRASSEN_F64_OZ_INT8, "oz_bf16": STRASSEN_F64_OZ_BF16}
@@ -52,8 +53,10 @@ def _ld(t):
     return max(t.stride(0), t.size(1), 1)
 
 
-def gemm(A, B, C, levels: int = 1, variant="ABC", dtype="f64", stream=None) -> None:
-    """In place on the stream: C += A @ B with ``levels`` levels of Strassen."""
+def gemm(A, B, C, levels: int = 1, variant="ABC", dtype="f64", stream=None, deterministic: bool = False) -> None:
+    """In place on the stream: C += A @ B with ``levels`` levels of Strassen.  With
+    ``deterministic`` the call goes through strassen_dgemm_ex with
+    STRASSEN_FLAG_DETERMINISTIC (fixed rounding order)."""
     A, B, C = _mat(A, "A"), _mat(B, "B"), _mat(C, "C")
     m, k = A.shape
     k2, n = B.shape
@@ -61,6 +64,11 @@ def gemm(A, B, C, levels: int = 1, variant="ABC", dtype="f64", stream=None) -> N
         raise ValueError(f"shape mismatch: A {tuple(A.shape)}, B {tuple(B.shape)}, C {tuple(C.shape)}")
     v = VARIANTS[variant.upper()] if isinstance(variant, str) else int(variant)
     d = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+    if deterministic:
+        st = strassen_dgemm_ex(0, 0, m, n, k, 1.0, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), 1.0, C.data_ptr(),
+                               _ld(C), int(levels), v, d, STRASSEN_FLAG_DETERMINISTIC, _stream(stream))
+        _binding._check(st, "strassen_dgemm_ex")
+        return
     st = strassen_gemm(m, n, k, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
                        int(levels), v, d, _stream(stream))
     _binding._check(st, "strassen_gemm")

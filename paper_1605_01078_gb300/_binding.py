@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libstrassen_gb300.so")
 # enums of strassen.h
 STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE, STRASSEN_AUTO = 0, 1, 2, 3
 STRASSEN_F64, STRASSEN_F64_OZ_INT8, STRASSEN_F64_OZ_BF16 = 0, 1, 2
+STRASSEN_FLAG_DETERMINISTIC = 1
 MAX_LEVELS, MAX_TERMS = 3, 8   # STRASSEN_MAX_LEVELS, STRASSEN_MAX_TERMS
 
 STATUS = {
@@ -54,6 +55,8 @@ SIGNATURES = {
     "strassen_plan_table": (_I, [_I, _I, _IP, _IP, _IP, _IP, _IP, _IP]),
     "strassen_dgemm": (_I, [_I, _I, _I64, _I64, _I64, ctypes.c_double, _P, _I64, _P, _I64, ctypes.c_double,
                             _P, _I64, _I, _I, _I, _P]),
+    "strassen_dgemm_ex": (_I, [_I, _I, _I64, _I64, _I64, ctypes.c_double, _P, _I64, _P, _I64, ctypes.c_double,
+                               _P, _I64, _I, _I, _I, ctypes.c_uint, _P]),
     "strassen_gemm_ab_noalloc": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _P]),
     "strassen_device_status": (_I, [_P]),
     "strassen_tune_record": (_I, [_I64, _I64, _I64, _I, _I, _I, _I]),
@@ -67,6 +70,8 @@ SIGNATURES = {
     "strassen_selector_use": (_I, [_I, _I]),
     "strassen_selector_clear": (_I, []),
     "strassen_check_wait_timeout": (_I, [_I64, _P]),
+    "strassen_profile_split_precision": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I,
+                                              ctypes.POINTER(ctypes.c_float), _P]),
     "strassen_check_int_fadd": (_I, [_I64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _P]),
 }
 
@@ -112,6 +117,13 @@ def strassen_dgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
                                 dtype, stream)
 
 
+def strassen_dgemm_ex(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, dtype,
+                      flags, stream) -> int:
+    """strassen_dgemm with flags (STRASSEN_FLAG_DETERMINISTIC); returns the status."""
+    return lib().strassen_dgemm_ex(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant,
+                                   dtype, flags, stream)
+
+
 def strassen_gemm_ab_noalloc(m, n, k, A, lda, B, ldb, C, ldc, levels, stream) -> int:
     """AB Strassen with its temporary in the library's fixed device array: no device
     allocation in the call (for callers that cannot allocate while they run)."""
@@ -136,6 +148,15 @@ def strassen_check_int_fadd(count, seed, stream=0) -> int:
     mm = ctypes.c_uint64(0)
     _check(lib().strassen_check_int_fadd(count, seed, ctypes.byref(mm), stream), "strassen_check_int_fadd")
     return mm.value
+
+
+def strassen_profile_split_precision(m, n, k, A, lda, B, ldb, C, ldc, levels, stream):
+    """One split-precision product C += A*B with CUDA events between its stages;
+    returns the milliseconds of (splits, slice products, recombination)."""
+    ms = (ctypes.c_float * 3)()
+    _check(lib().strassen_profile_split_precision(m, n, k, A, lda, B, ldb, C, ldc, levels, ms, stream),
+           "strassen_profile_split_precision")
+    return tuple(float(x) for x in ms)
 
 
 def strassen_select(m, n, k, dtype):

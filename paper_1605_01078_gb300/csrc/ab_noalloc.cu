@@ -49,9 +49,10 @@ cudaError_t scratch_address(double** out) {
 
 using namespace sgb;
 
-extern "C" int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
-                                        const double* B, int64_t ldb, double* C, int64_t ldc, int levels,
-                                        strassen_stream_t stream) {
+namespace {
+
+int ab_noalloc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double* C, int64_t ldc, int levels, strassen_stream_t stream) {
   if (levels < 1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if (m == 0 || n == 0 || k == 0) return STRASSEN_OK;
@@ -101,4 +102,17 @@ extern "C" int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k, const d
       return STRASSEN_ERR_CUDA;
   }
   return STRASSEN_OK;
+}
+
+}  // namespace
+
+extern "C" int strassen_gemm_ab_noalloc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                                        const double* B, int64_t ldb, double* C, int64_t ldc, int levels,
+                                        strassen_stream_t stream) {
+  // No exception may leave a C entry point (the set-up takes a lock, which can throw).
+  try {
+    return ab_noalloc(m, n, k, A, lda, B, ldb, C, ldc, levels, stream);
+  } catch (...) {
+    return STRASSEN_ERR_CUDA;
+  }
 }

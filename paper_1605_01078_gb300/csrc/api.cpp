@@ -15,11 +15,6 @@ using namespace sgb;
 
 namespace {
 
-int deterministic_requested() {
-  const char* v = std::getenv("STRASSEN_DETERMINISTIC");
-  return v && v[0] && v[0] != '0';
-}
-
 // Shared argument checks of strassen_gemm / classical_gemm.  Returns 1 when the call
 // has nothing to do, 0 when it should proceed, or a negative status.
 int check_args(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
@@ -39,10 +34,12 @@ int check_args(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, co
   return 0;
 }
 
-// BLAS options of strassen_dgemm: op(A), op(B) and the scale of the product.
+// BLAS options of strassen_dgemm_ex: op(A), op(B), the scale of the product, and
+// whether the rounding order must be the same on every run (STRASSEN_FLAG_DETERMINISTIC).
 struct Op {
   int ta = 0, tb = 0;
   double alpha = 1.0;
+  int det = 0;
 };
 
 // Argument checks of strassen_dgemm (stored shapes follow the transposes).  Returns 1
@@ -83,7 +80,7 @@ int run_classical(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
   L.epi = owner_epi;
   L.tile = tile;
   L.trans_a = op.ta; L.trans_b = op.tb; L.alpha = op.alpha;
-  choose_fp64_schedule(&L, deterministic_requested());
+  choose_fp64_schedule(&L, op.det);
   if (owner_epi == kEpiStore) {
     // The kernel accumulates into its target: a store is a clear followed by the adds.
     if (cudaMemset2DAsync(C, sizeof(double) * ldc, 0, sizeof(double) * n, m, s) != cudaSuccess)
@@ -98,7 +95,7 @@ int run_abc(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const
   L.epi = kEpiAtomicAdd;
   L.tile = tile;
   L.trans_a = op.ta; L.trans_b = op.tb; L.alpha = op.alpha;
-  choose_fp64_schedule(&L, deterministic_requested());
+  choose_fp64_schedule(&L, op.det);
   return cuda_status(launch_fp64(L, s));
 }
 
@@ -132,7 +129,7 @@ int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
     L.epi = kEpiStore;
     L.tile = tile;
     L.trans_a = op.ta; L.trans_b = op.tb;  // alpha is applied by the C updates
-    choose_fp64_schedule(&L, deterministic_requested());
+    choose_fp64_schedule(&L, op.det);
     // The kernel accumulates into M: clear it first.
     if (cudaMemsetAsync(M, 0, sizeof(double) * hm * hn, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
     cudaError_t e = launch_fp64(L, s);
@@ -165,7 +162,9 @@ int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, con
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
     e = launch_block_sum(V, hk, hn, B, ldb, k, n, hk, hn, pl.tb[r], pl.nb[r], s, op.tb);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
-    int st = run_classical(hm, hn, hk, X, hk, V, hn, M, hn, kEpiStore, s, tile);
+    Op inner;
+    inner.det = op.det;
+    int st = run_classical(hm, hn, hk, X, hk, V, hn, M, hn, kEpiStore, s, tile, inner);
     if (st != STRASSEN_OK) return st;
     e = launch_combine(C, ldc, m, n, M, hm, hn, pl.tc[r], pl.nc[r], s, op.alpha);
     if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
@@ -238,16 +237,18 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
   }
 }
 
-int strassen_dgemm(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
-                   int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int levels,
-                   strassen_variant variant, strassen_dtype dtype, strassen_stream_t stream) {
+int strassen_dgemm_ex(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                      int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int levels,
+                      strassen_variant variant, strassen_dtype dtype, unsigned flags, strassen_stream_t stream) {
   try {
     if (transa < 0 || transa > 1 || transb < 0 || transb > 1) return STRASSEN_ERR_ARG;
+    if (flags & ~(unsigned)STRASSEN_FLAG_DETERMINISTIC) return STRASSEN_ERR_ARG;
     if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
     if ((int)variant < 0 || (int)variant > 3) return STRASSEN_ERR_UNSUPPORTED;
     if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
     Op op;
     op.ta = transa; op.tb = transb; op.alpha = alpha;
+    op.det = (flags & STRASSEN_FLAG_DETERMINISTIC) ? 1 : 0;
     const int chk = check_args_op(m, n, k, A, lda, B, ldb, C, ldc, op);
     if (chk < 0) return chk;
     if (m == 0 || n == 0) return STRASSEN_OK;
@@ -260,6 +261,13 @@ int strassen_dgemm(int transa, int transb, int64_t m, int64_t n, int64_t k, doub
   } catch (...) {
     return STRASSEN_ERR_ALLOC;
   }
+}
+
+int strassen_dgemm(int transa, int transb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc, int levels,
+                   strassen_variant variant, strassen_dtype dtype, strassen_stream_t stream) {
+  return strassen_dgemm_ex(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant, dtype, 0u,
+                           stream);
 }
 
 int classical_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
@@ -378,6 +386,44 @@ int strassen_check_int_fadd(int64_t count, uint64_t seed, uint64_t* mismatches, 
   if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
   *mismatches = (uint64_t)mm;
   return STRASSEN_OK;
+}
+
+int strassen_profile_split_precision(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                                     int64_t ldb, double* C, int64_t ldc, int levels, float* stage_ms,
+                                     strassen_stream_t stream) {
+  try {
+    if (!stage_ms) return STRASSEN_ERR_NULL;
+    if (levels < 0 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
+    const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
+    if (chk < 0) return chk;
+    stage_ms[0] = stage_ms[1] = stage_ms[2] = 0.0f;
+    if (chk == 1) return STRASSEN_OK;
+    levels = clamp_levels(levels, m, n, k);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int st = STRASSEN_OK;
+    for (int i = 0; i < 4 && st == STRASSEN_OK; ++i)
+      if (cudaEventCreate(&ev[i]) != cudaSuccess) st = STRASSEN_ERR_CUDA;
+    if (st == STRASSEN_OK) {
+      Workspace ws;
+      ws.s = s;
+      if (cudaMallocAsync(&ws.p, (size_t)ozaki_workspace_bytes(m, n, k, levels), s) != cudaSuccess) {
+        cudaGetLastError();
+        ws.p = nullptr;
+        st = STRASSEN_ERR_ALLOC;
+      } else {
+        st = cuda_status(run_ozaki(m, n, k, A, lda, B, ldb, C, ldc, levels, ws.p, s, 0, 0, 1.0, ev));
+      }
+    }
+    if (st == STRASSEN_OK && cudaEventSynchronize(ev[3]) != cudaSuccess) st = STRASSEN_ERR_CUDA;
+    for (int i = 0; i < 3 && st == STRASSEN_OK; ++i)
+      if (cudaEventElapsedTime(&stage_ms[i], ev[i], ev[i + 1]) != cudaSuccess) st = STRASSEN_ERR_CUDA;
+    for (int i = 0; i < 4; ++i)
+      if (ev[i]) cudaEventDestroy(ev[i]);
+    return st;
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
 }
 
 int strassen_check_wait_timeout(int64_t limit_cycles, strassen_stream_t stream) {

@@ -16,8 +16,15 @@
 //       3.3); TMA zero-fills past the matrix edge.
 //   consumer warps (8)  accumulate M_tile += A_sum * B_sum with FP64 fused
 //       multiply-adds on a (BT/16) x (BT/16) register tile per thread and, after the
-//       last k-step of a unit, add gamma_q * alpha * M_tile into every C block q the
-//       product updates -- the fused scatter of the micro-kernel (Section 3.4).
+//       last k-step of a partial sum, add gamma_q * alpha * M_tile into every C block q
+//       the product updates -- the fused scatter of the micro-kernel (Section 3.4).
+//       A partial sum covers at most accumulation_chunk_k(L) of k (256, or 128 at
+//       three levels): a register accumulator that ran over all of h_k would add
+//       thousands of terms in sequence, and its rounding error, growing with the
+//       length of that sequence, set the error of the large products (about 2.4e-12
+//       of max|A| max|B| at 16384^3 with two levels, measured).  Chunks start from zero
+//       and are added into C, which shortens every sequential sum to the chunk length
+//       plus the number of chunks.
 //
 // C updates are device atomics (red.global.add.f64) for every schedule; a store into a
 // temporary is a clear followed by adds.  The two groups hand tiles over through
@@ -103,6 +110,7 @@ struct alignas(128) ProbDesc {
   int32_t epi;
   int32_t tiles_m, tiles_n, ksteps;
   int32_t use_tma;
+  int32_t flush_steps;       // k-steps per accumulation chunk (partial sums leave the registers)
   int32_t trans_a, trans_b;  // op(A) = A^T (A stored k x m), op(B) = B^T (B stored n x k)
   double alpha;              // the product is scaled by alpha in the scatter
 };
@@ -122,7 +130,7 @@ struct KArgs {
 // What the producers tell the consumers about the k-step in a summed slot.
 struct StepMeta {
   int p, r, t;  // problem, product, tile of the step
-  int flags;    // kStepLast: the last k-step of this block's part of the unit; kStepEnd: no step
+  int flags;    // kStepLast: the step ends a partial sum (see cursor_last); kStepEnd: no step
 };
 constexpr int kStepLast = 1, kStepEnd = 2;
 
@@ -261,10 +269,13 @@ __device__ Cursor range_cursor(const KArgs& a, int64_t id) {
   return c;
 }
 
+// True when the k-step ends a partial sum: the unit's last k-step, the end of this
+// block's share of a unit split by stream-K, or the end of an accumulation chunk.
 template <bool BATCHED>
 __device__ __forceinline__ bool cursor_last(const KArgs& a, const Cursor& c) {
   const ProbDesc& d = desc_of<BATCHED>(a, c.p);
-  return c.ks == d.ksteps - 1 || ((BATCHED || a.sched == kSchedStreamK) && c.left == 1);
+  return c.ks == d.ksteps - 1 || (c.ks + 1) % d.flush_steps == 0 ||
+         ((BATCHED || a.sched == kSchedStreamK) && c.left == 1);
 }
 
 template <bool BATCHED>
@@ -812,6 +823,7 @@ void fill_desc(const Fp64Launch& L, ProbDesc* d) {
   d->trans_a = L.trans_a;
   d->trans_b = L.trans_b;
   d->alpha = L.alpha;
+  d->flush_steps = accumulation_chunk_k(L.levels) / BK;
   // The innermost TMA coordinate is a block offset along k (A), n (B), m (A^T) or k
   // (B^T) plus a multiple of the tile: those block edges must be even.
   const bool edges_even = L.levels == 0 || (L.hk % 2 == 0 && L.hn % 2 == 0 && (!L.trans_a || L.hm % 2 == 0));

@@ -95,6 +95,14 @@ cudaError_t check_int_fadd(long long count, unsigned long long seed, unsigned lo
 // for the SM count).
 void choose_fp64_schedule(Fp64Launch* L, int prefer_deterministic);
 
+// Length along k of one partial sum of the FP64 product kernel (a multiple of its
+// k-step of 8): each consumer thread adds at most this many products in sequence
+// before the partial sum leaves its registers for C (or M).  Shorter chunks cut the
+// rounding error of long sums (which grows with the sequence length) at the cost of
+// more C updates per tile; deeper tables get shorter chunks, their products being
+// sums of more terms.
+inline int accumulation_chunk_k(int levels) { return levels >= 3 ? 128 : 256; }
+
 // Tile edge of a tile id (0: 128, 1: 64) and the number of tile ids.
 constexpr int kNumTiles = 2;
 inline int tile_edge_of(int tile_id) { return tile_id == 0 ? 128 : 64; }
@@ -128,9 +136,11 @@ int device_sm_count();
 // tensor-core slice products, recombine + scatter) on caller-provided workspace, and
 // the read-and-clear of its device status word.
 int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels);
+// With stage_events (four events), records them before the splits, before and after
+// the slice products, and after the recombination.
 cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                       double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream, int trans_a = 0,
-                      int trans_b = 0, double alpha = 1.0);
+                      int trans_b = 0, double alpha = 1.0, cudaEvent_t* stage_events = nullptr);
 int ozaki_device_status();
 
 // Learned selector (mlp.cu): argmin of the loaded MLP's predictions for a shape;

@@ -769,7 +769,7 @@ int ozaki_device_status() {
 
 cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                       double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream, int trans_a, int trans_b,
-                      double alpha) {
+                      double alpha, cudaEvent_t* stage_events) {
   std::call_once(g_oz_once, oz_init);
   if (g_oz_init != cudaSuccess) return g_oz_init;
   int sms = device_sm_count();
@@ -797,6 +797,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                                          (int)row_smem);
     if (e != cudaSuccess) return e;
   }
+  if (stage_events && cudaEventRecord(stage_events[0], stream) != cudaSuccess) return cudaGetLastError();
   oz_split_rows<<<dim3((unsigned)hmp, (unsigned)P), 256, row_smem, stream>>>(sa);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -831,8 +832,10 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n * ga.nseg;
   const int grid = (int)std::min<int64_t>(sms, units);
   void* gargs[] = {&ga};
+  if (stage_events && (e = cudaEventRecord(stage_events[1], stream)) != cudaSuccess) return e;
   e = cudaLaunchKernel((const void*)oz_gemm, dim3(grid), dim3(kThreads), gargs, oz_gemm_smem(), stream);
   if (e != cudaSuccess) return e;
+  if (stage_events && (e = cudaEventRecord(stage_events[2], stream)) != cudaSuccess) return e;
 
   RecombineArgs ra;
   ra.C = C; ra.ldc = ldc; ra.m = m; ra.n = n;
@@ -858,7 +861,9 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>(m, (int64_t)sms * 8);
   oz_recombine_scatter<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, stream>>>(ra);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && stage_events) e = cudaEventRecord(stage_events[3], stream);
+  return e;
 }
 
 }  // namespace sgb

@@ -39,6 +39,9 @@ int main(void) {
   if (strassen_dgemm(1, 0, 8, 4, 4, 1.0, (const double*)0x1000, 4, (const double*)0x2000, 4, 1.0,
                      (double*)0x3000, 4, 1, STRASSEN_ABC, STRASSEN_F64, 0) != STRASSEN_ERR_LD)
     return fail("dgemm ld check");
+  if (strassen_dgemm_ex(0, 0, 4, 4, 4, 1.0, (const double*)0x1000, 4, (const double*)0x2000, 4, 1.0,
+                        (double*)0x3000, 4, 1, STRASSEN_ABC, STRASSEN_F64, 4u, 0) != STRASSEN_ERR_ARG)
+    return fail("dgemm_ex flags check");
   if (strassen_workspace_size(4096, 4096, 4096, 1, STRASSEN_AB, STRASSEN_F64) != 8LL * 2048 * 2048)
     return fail("AB workspace");
   if (strassen_workspace_size(4096, 4096, 4096, 2, STRASSEN_ABC, STRASSEN_F64) != 0) return fail("ABC workspace");

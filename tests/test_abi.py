@@ -130,6 +130,18 @@ def test_dgemm_argument_checks_on_the_host():
     assert f(0, 0, 4, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 5, 0, 0, 0) == -4
 
 
+def test_dgemm_ex_flags_checked_on_the_host():
+    """strassen_dgemm_ex takes only the flags it defines; its argument checks are those
+    of strassen_dgemm."""
+    f = sg.strassen_dgemm_ex
+    assert sg.STRASSEN_FLAG_DETERMINISTIC == 1
+    assert f(0, 0, 4, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 2, 0) == -9
+    assert f(0, 0, 4, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 0x80000000, 0) == -9
+    assert f(0, 0, -1, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 1, 0) == -1
+    assert f(1, 0, 8, 4, 4, 1.0, P, 4, 2 * P, 4, 1.0, 3 * P, 4, 1, 0, 0, 1, 0) == -2
+    assert f(0, 0, 0, 4, 4, 1.0, 0, 4, 0, 4, 1.0, 0, 4, 1, 0, 0, 1, 0) == 0
+
+
 def test_plain_c_client_compiles_and_runs(tmp_path):
     """The header is plain C (extern "C", C types only): a C99 program includes it, links
     the library and calls its host-side entry points."""

@@ -196,6 +196,20 @@ def test_strassen_sampled_equals_full_recursion(levels, m, n, k):
         assert np.array_equal(got, full)
 
 
+def test_timing_build_computes_the_same_entries():
+    """The OpenMP timing build splits rows over threads but computes every entry with
+    the same operations: bit for bit the result of the plain build."""
+    A, B, C = W.uniform(130, 97, 1), W.uniform(97, 111, 2), W.uniform(130, 111, 3)
+    for L in (0, 1, 2):
+        ref = C.copy()
+        oracle.strassen(A, B, ref, L)
+        for threads in (1, 3):
+            got = C.copy()
+            oracle.strassen_timed(A, B, got, L, threads)
+            assert np.array_equal(got, ref)
+    assert oracle.host_cores() >= 1
+
+
 def test_strassen_sampled_exact_on_integers_and_strided_operands():
     A = W.integer(23, 19, 4, ld=25)
     B = W.integer(19, 17, 5, ld=20)
@@ -342,3 +356,39 @@ def test_dgemm_reduces_to_gemm_and_respects_beta_zero():
     assert np.array_equal(oracle.dgemm(0, 0, 1.0, A, B, 0.0, Cnan), A @ B)
     assert np.array_equal(oracle.dgemm(1, 1, 2.0, A.T.copy(), B.T.copy(), 0.0, Cnan), 2 * (A @ B))
     assert np.array_equal(oracle.dgemm(0, 0, 0.0, A, B, 0.5, C), 0.5 * C)
+
+
+# ---------------------------------------------------------------- symmetric rank-k update
+
+@pytest.mark.parametrize("uplo", [0, 1])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_dsyrk_definition_on_integers(uplo, trans):
+    """alpha op(A) op(A)^T + beta C on one triangle, against brute force in exact
+    integers; the other triangle is returned untouched (NaN stays NaN)."""
+    n, k = 11, 7
+    A = W.integer(k, n, 3) if trans else W.integer(n, k, 3)
+    C = W.integer(n, n, 4)
+    i, j = np.indices((n, n))
+    tri = (j <= i) if uplo == 0 else (j >= i)
+    C[~tri] = np.nan
+    Aop = np.ascontiguousarray(A.T if trans else A)
+    P = brute(Aop, np.ascontiguousarray(Aop.T), np.zeros((n, n)))
+    out = oracle.dsyrk(uplo, trans, 2.0, A, -3.0, C)
+    assert np.array_equal(out[tri], (2.0 * P - 3.0 * C)[tri])
+    assert np.all(np.isnan(out[~tri]))
+
+
+def test_dsyrk_triangles_are_transposes_and_beta_zero_ignores_c():
+    n, k = 9, 13
+    A = W.integer(n, k, 5)
+    C = W.integer(n, n, 6)
+    C = C + C.T  # symmetric
+    lo = oracle.dsyrk(0, 0, 1.0, A, 1.0, C)
+    up = oracle.dsyrk(1, 0, 1.0, A, 1.0, C)
+    assert np.array_equal(np.tril(lo), np.tril(up.T))
+    Cn = np.full((n, n), np.nan)
+    z = oracle.dsyrk(0, 0, 1.0, A, 0.0, Cn)
+    assert np.array_equal(np.tril(z), np.tril(brute(A, np.ascontiguousarray(A.T), np.zeros((n, n)))))
+    # k = 0: only the scaling by beta
+    e = oracle.dsyrk(1, 0, 5.0, np.zeros((n, 0)), 2.0, C)
+    assert np.array_equal(np.triu(e), np.triu(2.0 * C))

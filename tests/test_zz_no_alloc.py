@@ -7,10 +7,12 @@ out-of-memory path).  Its temporary lives in one fixed array inside the library 
 keeps the previous call's contents, so every case here makes two calls in a row and
 checks both against the regular AB entry point: bit for bit on integer-valued inputs,
 and within the float tolerance the other GPU tests use (1e-13 at one level, 1e-12 at
-two, normwise) on uniform[-1, 1] inputs.
+two and three, max|C1 - C2| / (max|A| max|B|)) on uniform[-1, 1] inputs.
 
 This file is collected last on purpose; it passes alone in a fresh process as well.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -21,7 +23,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 1e-13, 2: 1e-12}
+TOL = {1: 1e-13, 2: 1e-12, 3: 1e-12}
 SCRATCH_ELEMS = 1 << 22  # doubles in the library's fixed array
 
 
@@ -49,8 +51,8 @@ def no_alloc(A, B, C0, levels):
     return C
 
 
-def normwise(C, R, A):
-    den = float(torch.max(torch.sum(torch.abs(A), dim=1)))
+def strict(C, R, A, B):
+    den = float(torch.max(torch.abs(A))) * float(torch.max(torch.abs(B)))
     return float(torch.max(torch.abs(C - R))) / den
 
 
@@ -76,7 +78,7 @@ def test_no_alloc_matches_ab_two_calls_in_a_row(m, n, k, levels, integer):
         if integer:
             assert torch.equal(got, ref)
         else:
-            assert normwise(got, ref, A) <= TOL[levels]
+            assert strict(got, ref, A, B) <= TOL[levels]
 
 
 def test_no_alloc_after_a_larger_call_is_unaffected():
@@ -88,7 +90,7 @@ def test_no_alloc_after_a_larger_call_is_unaffected():
         got = no_alloc(A, B, C0, 1)
         ref = regular_ab(A, B, C0, 1)
         torch.cuda.synchronize()
-        assert normwise(got, ref, A) <= TOL[1]
+        assert strict(got, ref, A, B) <= TOL[1]
 
 
 def test_no_alloc_rejects_products_beyond_the_array():
@@ -104,3 +106,55 @@ def test_no_alloc_rejects_products_beyond_the_array():
     torch.cuda.synchronize()
     assert torch.all(C == 5.0)
     assert sg.strassen_gemm_ab_noalloc(m, n, k, A.data_ptr(), k, B.data_ptr(), n, C.data_ptr(), n, 4, 0) == -4
+
+
+def _cudart():
+    """The CUDA runtime the library is linked against (found among the loaded objects)."""
+    sg.load_library()
+    paths = []
+    with open("/proc/self/maps") as fh:
+        for line in fh:
+            path = line.split()[-1]
+            if "libcudart.so" in path and path not in paths:
+                paths.append(path)
+    if not paths:
+        pytest.skip("no CUDA runtime among the loaded objects")
+    return ctypes.CDLL(paths[0])
+
+
+def test_no_alloc_call_makes_no_device_allocation():
+    """The library's temporaries come from the device's current memory pool
+    (cudaMallocAsync).  With the pool's high-water mark reset before each call, a
+    no-allocation call must leave it at the memory in use before the call, while the
+    regular AB call must raise it by at least its temporary M (so the probe does see the
+    library's allocations)."""
+    rt = _cudart()
+    USED_CURRENT, USED_HIGH = 0x7, 0x8  # cudaMemPoolAttrUsedMemCurrent / UsedMemHigh
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetMemPool(ctypes.byref(pool), ctypes.c_int(torch.cuda.current_device())) == 0
+
+    def attr(a):
+        v = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolGetAttribute(pool, ctypes.c_int(a), ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high():
+        zero = ctypes.c_uint64(0)
+        assert rt.cudaMemPoolSetAttribute(pool, ctypes.c_int(USED_HIGH), ctypes.byref(zero)) == 0
+
+    m = n = k = 1536
+    A, B, C0 = dev(W.uniform(m, k, 11)), dev(W.uniform(k, n, 12)), dev(W.uniform(m, n, 13))
+    no_alloc(A, B, C0, 1)  # first call on this device: its set-up
+    for levels in (1, 2):
+        torch.cuda.synchronize()
+        before = attr(USED_CURRENT)
+        reset_high()
+        got = no_alloc(A, B, C0, levels)
+        torch.cuda.synchronize()
+        assert attr(USED_HIGH) == before, "the no-allocation call allocated from the pool"
+        reset_high()
+        ref = regular_ab(A, B, C0, levels)
+        torch.cuda.synchronize()
+        h = -(-m // 2 ** levels)
+        assert attr(USED_HIGH) >= before + 8 * h * h, "the probe did not see the regular call's temporary"
+        assert strict(got, ref, A, B) <= TOL[levels]
