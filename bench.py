@@ -407,7 +407,8 @@ def bench_other_levels(sg, torch, W, n, levels_list, variant="ABC", reps=3, accu
     fraction (CUDA events per call), and the sampled strict error of one call next to
     the textbook Strassen's."""
     Ah, Bh, Ch = W.uniform(n, n, 100), W.uniform(n, n, 101), W.uniform(n, n, 102)
-    A, B, C = torch.from_numpy(Ah).cuda(), torch.from_numpy(Bh).cuda(), torch.from_numpy(Ch).cuda()
+    A, B, C0 = torch.from_numpy(Ah).cuda(), torch.from_numpy(Bh).cuda(), torch.from_numpy(Ch).cuda()
+    C = C0.clone()  # the timed calls accumulate into C; the error checks start from C0
     stream = torch.cuda.current_stream()
     rows, cols = W.sample_indices(n, n, ERR_SAMPLES // 2, 7)
     ri, ci = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
@@ -415,7 +416,7 @@ def bench_other_levels(sg, torch, W, n, levels_list, variant="ABC", reps=3, accu
     for lv in levels_list:
         err = None
         if accuracy:
-            C1 = C.clone()
+            C1 = C0.clone()
             sg.gemm(A, B, C1, levels=lv, variant=variant, stream=stream)
             got = C1[ri, ci].cpu().numpy()
             del C1
@@ -425,7 +426,7 @@ def bench_other_levels(sg, torch, W, n, levels_list, variant="ABC", reps=3, accu
         out[str(lv)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3, "n": n,
                         "variant": variant, "algorithmic_gflops": alg, "frac": alg / FP64_PEAK_GFLOPS,
                         "error": err}
-    del A, B, C
+    del A, B, C, C0
     torch.cuda.empty_cache()
     return out
 

@@ -197,6 +197,34 @@ STRASSEN_API int strassen_dgemm_ex(int transa, int transb, int64_t m, int64_t n,
                                    double* C, int64_t ldc, int levels, strassen_variant variant,
                                    strassen_dtype dtype, unsigned flags, strassen_stream_t stream);
 
+/*
+ * strassen_dsyrk -- the symmetric rank-k update C = alpha op(A) op(A)^T + beta C on one
+ * triangle of C (the BLAS DSYRK operation, row-major), with the Strassen family doing
+ * the off-diagonal products: the paper's conclusion names the other level-3 BLAS
+ * operations as users of the same fused Strassen kernels.
+ *
+ *   uplo     0: the lower triangle (j <= i, diagonal included) is updated; 1: the upper
+ *            (j >= i).  Elements of C outside that triangle are neither read nor written.
+ *   trans    0: op(A) = A, A stored n x k (lda >= k); 1: op(A) = A^T, A stored k x n
+ *            (lda >= n).  Transposed operands are read in place.
+ *   n, k     C is n x n (ldc >= n); k >= 0.
+ *   alpha, beta   beta = 0 sets the triangle to alpha op(A) op(A)^T without reading it;
+ *            alpha = 0 or k = 0 only scales the triangle.
+ *   levels   Strassen levels of the off-diagonal products (-1: the selector's choice for
+ *            each product); the diagonal blocks are classical.
+ *   flags    0 or STRASSEN_FLAG_DETERMINISTIC (as strassen_dgemm_ex).
+ *
+ * Method: the triangle is scaled by beta; then, recursively, C = [C00 .; C10 C11] (lower)
+ * with a split n0 near n/2 (a multiple of 128 where possible): C00 and C11 by the same
+ * recursion, C10 += alpha op(A)[n0:] op(A)[:n0]^T by the Strassen product (the upper
+ * triangle takes C01 instead); blocks of at most 1024 rows are one classical launch whose
+ * epilogue writes only the triangle.  C must not overlap A.  Returns STRASSEN_OK or a
+ * negative status (STRASSEN_ERR_ARG for uplo, trans or flags outside their values).
+ */
+STRASSEN_API int strassen_dsyrk(int uplo, int trans, int64_t n, int64_t k, double alpha, const double* A,
+                                int64_t lda, double beta, double* C, int64_t ldc, int levels, unsigned flags,
+                                strassen_stream_t stream);
+
 /* One problem of a batched call: C += A*B as in strassen_gemm. */
 typedef struct {
   int64_t m, n, k;
@@ -205,32 +233,38 @@ typedef struct {
   double* C;
   int64_t lda, ldb, ldc;
   int levels;               /* -1 = the autotuner's choice, else 0, 1, 2 or 3 */
-  strassen_variant variant; /* STRASSEN_AUTO = the autotuner's choice; AB and Naive run as ABC */
+  strassen_variant variant; /* STRASSEN_ABC or STRASSEN_AUTO (both run the fused ABC form);
+                               AB and Naive only with levels = 0 (classical) */
 } strassen_problem;
 
 /*
- * strassen_gemm_batched -- many independent products of uneven shapes in one
- * persistent kernel launch per block tile (the batching pattern; not in the paper).
+ * strassen_gemm_batched -- many independent products of uneven shapes in persistent
+ * kernel launches (the batching pattern; not in the paper).
  *
  *   count   number of problems (>= 0).
  *   probs   HOST array of `count` problems; each is validated as in strassen_gemm.
  *           The byte ranges [C, C + (m-1)*ldc + n) of different problems must not
  *           overlap (STRASSEN_ERR_ARG otherwise).  Every problem runs as ABC
- *           (levels 1-3) or classical (levels 0).  Each problem gets the block tile
- *           (128x128 or 64x64) with the smaller estimate of padded tile work, and
- *           with levels = -1 also the level (an exhaustive record for the shape,
- *           strassen_tune_record, takes precedence).  The problems of one tile share
- *           one persistent launch: the call makes one launch per tile in use (at
- *           most two).
+ *           (levels 1-3) or classical (levels 0); a problem asking for AB or Naive
+ *           with levels other than 0 returns STRASSEN_ERR_UNSUPPORTED.  Each problem
+ *           gets the block tile (128x128 or 64x64) with the smaller estimate of padded
+ *           tile work, and with levels = -1 also the level (an exhaustive record for
+ *           the shape, strassen_tune_record, takes precedence).
  *   dtype   STRASSEN_F64.
  *   stream  the CUDA stream.
  *
- * The problems are split into work units (problem, product, 128x128 tile, k-steps);
- * the thread blocks of one persistent launch take equal contiguous ranges of them
- * (stream-K) and add their partial products into C with device atomics.  The work
- * list travels in kernel parameters to a small kernel that writes it into a
- * stream-ordered temporary (cudaMallocAsync), so the whole call can be captured in a
- * CUDA graph and replayed.  Returns STRASSEN_OK or a negative status.
+ * Problems with the same tile and level share one persistent launch (the kernel
+ * instance sized for that level's term count), so the call makes one launch per
+ * (tile, level) group in use, at most eight.  Within a launch the work units (problem,
+ * product, tile, k-steps) are claimed in chunks from a counter, and partial products
+ * are added into C with device atomics.  With several groups the launches go largest
+ * first, alternately on `stream` and on a library stream forked from it with an event
+ * (so one launch's tail overlaps the next launch's start); `stream` waits for both
+ * before the call's work counts as done.  The work list travels in kernel parameters
+ * to a small kernel that writes it into a stream-ordered temporary (cudaMallocAsync),
+ * so the whole call can be captured in a CUDA graph and replayed; make one call on the
+ * device outside a capture first (it creates the library stream).  Returns STRASSEN_OK
+ * or a negative status.
  */
 STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
                           strassen_dtype dtype, strassen_stream_t stream);
@@ -242,15 +276,16 @@ STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
  * the paper builds its performance model for.  In order of precedence it returns
  *   1. the exhaustive-measurement record for exactly this shape and dtype, if one was
  *      stored with strassen_tune_record();
- *   2. the argmin of the learned selector's predictions, if a network was loaded with
- *      strassen_selector_load() (one small kernel launch on a library stream, then a
- *      wait for its result);
+ *   2. the argmin of the learned selector's predictions over its 20 candidates (every
+ *      level 0-3, variant and tile; see strassen_selector_candidate), if a network was
+ *      loaded with strassen_selector_load() and is enabled for the dtype.  The first
+ *      choice for a shape runs one small kernel on a library stream and waits for it;
+ *      the choice is cached, so later calls for the shape do no GPU work;
  *   3. the analytic model's argmin over levels 0 to 3, variants and tiles otherwise
  *      (FP64), or classical slices (split-precision dtypes).
- * The learned selector's candidates stop at two levels (its output layer has the 7
- * candidates listed below; the tile then follows the analytic model); exhaustive
- * records may hold any level and tile.  strassen_gemm with levels = -1 and
- * STRASSEN_AUTO runs exactly the selected (levels, variant, tile).
+ * strassen_gemm with levels = -1 and STRASSEN_AUTO runs exactly the selected
+ * (levels, variant, tile); inside a stream capture it uses the learned selector only for
+ * shapes already in its cache (no launch, no wait) and otherwise the model.
  * The model prefers fewer levels on ties within 1 %.
  *
  *   levels, variant, tile_id   outputs (host pointers, non-NULL).
@@ -282,17 +317,23 @@ STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int 
 
 /*
  * The learned selector (not in the paper; it stands in for the analytic model of
- * Section 4.2).  A multilayer perceptron 6 -> 64 -> 64 -> 7 (FP32, ReLU) maps the
- * features ((log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype one-hot) to the
- * predicted log2 seconds of the 7 candidates (levels, variant): 0 (0, ABC),
- * 1 (1, ABC), 2 (1, AB), 3 (1, Naive), 4 (2, ABC), 5 (2, AB), 6 (2, Naive).  Its
- * parameters are one float vector of strassen_mlp_param_count() entries:
- * [W1 (64x6 row-major), b1 (64), W2 (64x64), b2 (64), W3 (7x64), b3 (7)].
+ * Section 4.2).  A multilayer perceptron 26 -> 64 -> 64 -> 20 (FP32, ReLU) maps a
+ * shape's features to a correction of the analytic model's log2 seconds for each of
+ * STRASSEN_SELECTOR_CANDIDATES = 20 candidates; the selection is the argmin over the
+ * dtype's valid candidates of (model log2 seconds + correction).  Features, from
+ * strassen_selector_features: (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype
+ * one-hot, then for every candidate (model log2 seconds + 7)/7.  Candidates
+ * (strassen_selector_candidate): 0, 1 classical with tile 0, 1; 2 + 6 (L - 1) + 2 v + t
+ * for L levels (1-3), variant v (ABC, AB, Naive) and tile t.  The split-precision dtype
+ * uses the tile-0 ABC candidates (0, 2, 8, 14).  Its parameters are one float vector of
+ * strassen_mlp_param_count() entries: [W1 (64x26 row-major), b1 (64), W2 (64x64),
+ * b2 (64), W3 (20x64), b3 (20)].
  *
- * strassen_mlp_forward   Y[batch][7] = network(X[batch][6]); all DEVICE pointers.
+ * strassen_mlp_forward   Y[batch][20] = network(X[batch][26]); all DEVICE pointers.
  * strassen_mlp_loss_grad grad = d/dparams of sum mask (Y - T)^2 / mask_sum over the
- *                        batch (X [batch][6], T and mask [batch][7], DEVICE); grad is
- *                        overwritten.  mask_sum > 0 is the sum of mask.
+ *                        batch (X [batch][26], T and mask [batch][20], DEVICE); grad is
+ *                        overwritten.  mask_sum > 0 is the sum of mask.  For training,
+ *                        T = log2 measured seconds - the model's log2 seconds.
  * strassen_mlp_adam      one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1)
  *                        on `count` parameters with moment buffers m, v (DEVICE).
  * strassen_selector_load copies a trained parameter vector (HOST) to the current device
@@ -302,8 +343,15 @@ STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int 
  *                        (default: all enabled); with it disabled, strassen_select()
  *                        falls through to the analytic model for that dtype.  The tuning
  *                        driver enables it only where it beat the model on held-out shapes.
+ * strassen_selector_candidate  (levels, variant, tile_id) of candidate c (0..19).
+ * strassen_selector_features   x[26] (network inputs), base[20] (the model's log2
+ *                        seconds) and the bit mask of the candidates valid for `dtype`,
+ *                        on the host (no GPU work; the model reads the device's SM
+ *                        count and clock).
  * All return STRASSEN_OK or a negative status; the kernels run on `stream`.
  */
+#define STRASSEN_SELECTOR_CANDIDATES 20
+#define STRASSEN_SELECTOR_INPUTS 26
 STRASSEN_API int strassen_mlp_param_count(void);
 STRASSEN_API int strassen_mlp_forward(const float* params, const float* X, int batch, float* Y,
                                       strassen_stream_t stream);
@@ -315,6 +363,10 @@ STRASSEN_API int strassen_mlp_adam(float* params, const float* grad, float* m, f
 STRASSEN_API int strassen_selector_load(const float* params_host, int count);
 STRASSEN_API int strassen_selector_use(int dtype, int enable);
 STRASSEN_API int strassen_selector_clear(void);
+STRASSEN_API int strassen_selector_candidate(int candidate, int* levels, strassen_variant* variant,
+                                             int* tile_id);
+STRASSEN_API int strassen_selector_features(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, float* x,
+                                            float* base, unsigned* valid);
 
 /*
  * strassen_workspace_size -- bytes of stream-ordered temporaries a strassen_gemm call

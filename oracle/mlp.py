@@ -3,21 +3,24 @@
 Not a method of the paper: a small network standing in for the paper's analytical
 performance model (Section 4.2) in choosing a member of the family.  Definition:
 
-    x  (6)   features: (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype one-hot (3)
-    h1 = relu(W1 x + b1)      W1: 64 x 6
+    x  (26)  features: (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype one-hot (3),
+             then (b_c + 7)/7 for the 20 candidates, b_c the analytic model's log2 seconds
+    h1 = relu(W1 x + b1)      W1: 64 x 26
     h2 = relu(W2 h1 + b2)     W2: 64 x 64
-    y  = W3 h2 + b3           W3: 7 x 64   (predicted log2 seconds of each candidate)
+    y  = W3 h2 + b3           W3: 20 x 64  (the correction to b_c: predicted log2 seconds
+                                            of candidate c are b_c + y_c)
 
     loss = sum_{i,c} mask_ic (y_ic - t_ic)^2 / sum_{i,c} mask_ic
 
-with t the measured log2 seconds and mask 1 where a candidate was measured.  The flat
-parameter vector is [W1 (row-major), b1, W2, b2, W3, b3].
+with t the measured log2 seconds minus b, and mask 1 where a candidate was measured.
+The flat parameter vector is [W1 (row-major), b1, W2, b2, W3, b3].
 """
 from __future__ import annotations
 
 import numpy as np
 
-N_IN, N_H, N_OUT = 6, 64, 7
+N_SHAPE, N_OUT, N_H = 6, 20, 64
+N_IN = N_SHAPE + N_OUT
 SHAPES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
           ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
 N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
@@ -32,14 +35,17 @@ def unpack(theta: np.ndarray) -> dict:
     return out
 
 
-def features(m, n, k, dtype) -> np.ndarray:
-    """Feature rows for arrays of sizes and dtype codes (0 FP64, 1 INT8 split, 2 BF16 split)."""
-    m, n, k, dtype = (np.asarray(v) for v in (m, n, k, dtype))
+def features(m, n, k, dtype, base=None) -> np.ndarray:
+    """Feature rows for arrays of sizes, dtype codes (0 FP64, 1 INT8 split, 2 BF16 split)
+    and the model's log2 seconds per candidate `base` [rows, 20] (zeros when None)."""
+    m, n, k, dtype = (np.atleast_1d(np.asarray(v)) for v in (m, n, k, dtype))
     x = np.zeros((m.size, N_IN))
     x[:, 0] = (np.log2(m) - 11.0) / 3.0
     x[:, 1] = (np.log2(n) - 11.0) / 3.0
     x[:, 2] = (np.log2(k) - 11.0) / 3.0
     x[np.arange(m.size), 3 + dtype.astype(int)] = 1.0
+    b = np.zeros((m.size, N_OUT)) if base is None else np.asarray(base, dtype=np.float64).reshape(m.size, N_OUT)
+    x[:, N_SHAPE:] = (b + 7.0) / 7.0
     return x
 
 

@@ -18,14 +18,15 @@ from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  
                        STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_FLAG_DETERMINISTIC, STRASSEN_NAIVE,
                        StrassenError,
                        classical_gemm, strassen_gemm, strassen_gemm_ab_noalloc, strassen_gemm_batched,
-                       strassen_dgemm, strassen_dgemm_ex,
+                       strassen_dgemm, strassen_dgemm_ex, strassen_dsyrk,
                        strassen_plan_table,
                        strassen_problem, strassen_select, strassen_status_string, strassen_device_status,
                        strassen_check_wait_timeout, strassen_tune_record, strassen_tune_clear,
                        strassen_model_seconds, strassen_mlp_param_count, strassen_mlp_forward,
                        strassen_mlp_loss_grad, strassen_mlp_adam, strassen_selector_load,
                        strassen_selector_clear, strassen_check_int_fadd, strassen_selector_use,
-                       strassen_workspace_size, strassen_profile_split_precision)
+                       strassen_workspace_size, strassen_profile_split_precision,
+                       strassen_selector_candidate, strassen_selector_features)
 
 VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO}
 DTYPES = {"f64": STRASSEN_F64, "oz_int8": STRASSEN_F64_OZ_INT8, "oz_bf16": STRASSEN_F64_OZ_BF16}
@@ -89,6 +90,20 @@ def dgemm(A, B, C, alpha: float = 1.0, beta: float = 1.0, trans_a: bool = False,
     st = strassen_dgemm(int(bool(trans_a)), int(bool(trans_b)), m, n, k, float(alpha), A.data_ptr(), _ld(A),
                         B.data_ptr(), _ld(B), float(beta), C.data_ptr(), _ld(C), int(levels), v, d, _stream(stream))
     _binding._check(st, "strassen_dgemm")
+
+
+def dsyrk(A, C, alpha: float = 1.0, beta: float = 1.0, lower: bool = True, trans: bool = False, levels: int = -1,
+          deterministic: bool = False, stream=None) -> None:
+    """In place on the stream: one triangle of C becomes alpha op(A) op(A)^T + beta C,
+    op(A) = A.T when trans (A stored k x n)."""
+    A, C = _mat(A, "A"), _mat(C, "C")
+    n, k = (A.shape[1], A.shape[0]) if trans else (A.shape[0], A.shape[1])
+    if tuple(C.shape) != (n, n):
+        raise ValueError(f"shape mismatch: op(A) {n}x{k}, C {tuple(C.shape)}")
+    st = strassen_dsyrk(0 if lower else 1, int(bool(trans)), n, k, float(alpha), A.data_ptr(), _ld(A), float(beta),
+                        C.data_ptr(), _ld(C), int(levels), STRASSEN_FLAG_DETERMINISTIC if deterministic else 0,
+                        _stream(stream))
+    _binding._check(st, "strassen_dsyrk")
 
 
 def classical(A, B, C, stream=None) -> None:

@@ -58,6 +58,8 @@ SIGNATURES = {
     "strassen_dgemm_ex": (_I, [_I, _I, _I64, _I64, _I64, ctypes.c_double, _P, _I64, _P, _I64, ctypes.c_double,
                                _P, _I64, _I, _I, _I, ctypes.c_uint, _P]),
     "strassen_gemm_ab_noalloc": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I, _P]),
+    "strassen_dsyrk": (_I, [_I, _I, _I64, _I64, ctypes.c_double, _P, _I64, ctypes.c_double, _P, _I64, _I,
+                            ctypes.c_uint, _P]),
     "strassen_device_status": (_I, [_P]),
     "strassen_tune_record": (_I, [_I64, _I64, _I64, _I, _I, _I, _I]),
     "strassen_tune_clear": (_I, []),
@@ -69,6 +71,9 @@ SIGNATURES = {
     "strassen_selector_load": (_I, [ctypes.POINTER(ctypes.c_float), _I]),
     "strassen_selector_use": (_I, [_I, _I]),
     "strassen_selector_clear": (_I, []),
+    "strassen_selector_candidate": (_I, [_I, _IP, _IP, _IP]),
+    "strassen_selector_features": (_I, [_I64, _I64, _I64, _I, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint)]),
     "strassen_check_wait_timeout": (_I, [_I64, _P]),
     "strassen_profile_split_precision": (_I, [_I64, _I64, _I64, _P, _I64, _P, _I64, _P, _I64, _I,
                                               ctypes.POINTER(ctypes.c_float), _P]),
@@ -122,6 +127,11 @@ def strassen_dgemm_ex(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, l
     """strassen_dgemm with flags (STRASSEN_FLAG_DETERMINISTIC); returns the status."""
     return lib().strassen_dgemm_ex(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, levels, variant,
                                    dtype, flags, stream)
+
+
+def strassen_dsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, levels, flags, stream) -> int:
+    """C = alpha op(A) op(A)^T + beta C on one triangle; returns the status."""
+    return lib().strassen_dsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, levels, flags, stream)
 
 
 def strassen_gemm_ab_noalloc(m, n, k, A, lda, B, ldb, C, ldc, levels, stream) -> int:
@@ -204,6 +214,28 @@ def strassen_selector_use(dtype, enable) -> int:
 
 def strassen_selector_clear() -> int:
     return lib().strassen_selector_clear()
+
+
+SELECTOR_CANDIDATES, SELECTOR_INPUTS = 20, 26  # STRASSEN_SELECTOR_CANDIDATES / _INPUTS
+
+
+def strassen_selector_candidate(c):
+    """(levels, variant, tile_id) of the learned selector's candidate c."""
+    lv, var, tile = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().strassen_selector_candidate(c, ctypes.byref(lv), ctypes.byref(var), ctypes.byref(tile)),
+           "strassen_selector_candidate")
+    return lv.value, var.value, tile.value
+
+
+def strassen_selector_features(m, n, k, dtype):
+    """(x[26], base[20], valid mask) of a shape: the network's inputs, the analytic
+    model's log2 seconds per candidate and the candidates valid for the dtype."""
+    x = (ctypes.c_float * SELECTOR_INPUTS)()
+    base = (ctypes.c_float * SELECTOR_CANDIDATES)()
+    valid = ctypes.c_uint()
+    _check(lib().strassen_selector_features(m, n, k, dtype, x, base, ctypes.byref(valid)),
+           "strassen_selector_features")
+    return list(x), list(base), valid.value
 
 
 def strassen_workspace_size(m, n, k, levels, variant, dtype) -> int:

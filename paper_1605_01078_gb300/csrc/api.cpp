@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -184,6 +185,46 @@ int run_oz(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
   return cuda_status(run_ozaki(m, n, k, A, lda, B, ldb, C, ldc, levels, ws.p, s, op.ta, op.tb, op.alpha));
 }
 
+// A non-blocking library stream per device for the second branch of a batched call.
+cudaError_t side_stream(cudaStream_t* out) {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!streams[dev]) {
+    e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
+  *out = streams[dev];
+  return cudaSuccess;
+}
+
+// The selection of strassen_select (exhaustive record, then the learned selector, then
+// the analytic model or, for split precision, classical slices).  With may_launch = 0
+// the learned selector answers only from its cache of earlier choices (no kernel launch
+// and no wait), as inside a stream capture.
+void select_plan(int64_t m, int64_t n, int64_t k, int dtype, int may_launch, int* levels, strassen_variant* variant,
+                 int* tile_id) {
+  int lv = 0, var = STRASSEN_ABC, tile = 0, cand = -1;
+  if (record_lookup(m, n, k, dtype, &lv, &var, &tile)) {
+    // exhaustive measurement
+  } else if (m > 0 && n > 0 && k > 0 && mlp_select(m, n, k, dtype, may_launch, &cand)) {
+    selector_candidate(cand, &lv, &var, &tile);
+  } else if (dtype == STRASSEN_F64) {
+    model_select(m, n, k, &lv, &var, &tile);
+  } else {  // split precision: classical slices
+    lv = 0;
+    var = STRASSEN_ABC;
+    tile = 0;
+  }
+  *levels = lv;
+  *variant = (strassen_variant)var;
+  *tile_id = tile;
+}
+
 // The product C += alpha op(A) op(B) with the requested (or selected) plan; arguments
 // already checked.
 int run_product(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
@@ -194,8 +235,12 @@ int run_product(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, c
   if (levels == -1 || variant == STRASSEN_AUTO) {
     int sl = 0, st_tile = 0;
     strassen_variant sv = STRASSEN_ABC;
-    const int st = strassen_select(m, n, k, dtype, &sl, &sv, &st_tile);
-    if (st != STRASSEN_OK) return st;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+      cudaGetLastError();
+      cap = cudaStreamCaptureStatusActive;
+    }
+    select_plan(m, n, k, (int)dtype, cap == cudaStreamCaptureStatusNone, &sl, &sv, &st_tile);
     if (levels == -1 && variant == STRASSEN_AUTO) tile = st_tile;
     if (levels == -1) levels = sl;
     if (variant == STRASSEN_AUTO) variant = sv;
@@ -217,9 +262,87 @@ int run_product(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, c
   }
 }
 
+// Symmetric rank-k update, recursively: the diagonal blocks by the same recursion
+// down to kSyrkLeaf rows, where one classical launch writes only the triangle; the
+// off-diagonal block by the Strassen product with the transposed operand read in place.
+constexpr int64_t kSyrkLeaf = 1024;
+
+int run_syrk(int uplo, int trans, int64_t n, int64_t k, double alpha, const double* A, int64_t lda, double* C,
+             int64_t ldc, int levels, cudaStream_t s, int det) {
+  if (n <= 0) return STRASSEN_OK;
+  // Row r of op(A) (k long): A + r * lda for trans = 0, column r of A (A + r) for trans = 1.
+  auto row_block = [&](int64_t r0) { return trans ? A + r0 : A + r0 * lda; };
+  if (n <= kSyrkLeaf) {
+    Fp64Launch L = make_launch(n, n, k, A, lda, A, lda, C, ldc, 0);
+    L.trans_a = trans;       // op(A)
+    L.trans_b = 1 - trans;   // op(A)^T: the same storage read the other way
+    L.alpha = alpha;
+    L.tri = uplo == 0 ? 1 : 2;
+    L.epi = kEpiRmw;
+    choose_fp64_schedule(&L, det);
+    return cuda_status(launch_fp64(L, s));
+  }
+  // Split near the middle, on a multiple of 128 rows where one lies inside.
+  int64_t n0 = (n + 1) / 2;
+  if (n0 > 128) n0 = n0 / 128 * 128;
+  int st = run_syrk(uplo, trans, n0, k, alpha, A, lda, C, ldc, levels, s, det);
+  if (st != STRASSEN_OK) return st;
+  const int64_t n1 = n - n0;
+  st = run_syrk(uplo, trans, n1, k, alpha, row_block(n0), lda, C + n0 * ldc + n0, ldc, levels, s, det);
+  if (st != STRASSEN_OK) return st;
+  Op op;
+  op.alpha = alpha;
+  op.det = det;
+  // lower: C10 (n1 x n0) += alpha op(A)_1 op(A)_0^T; upper: C01 (n0 x n1) += alpha op(A)_0 op(A)_1^T
+  const double* Ar = uplo == 0 ? row_block(n0) : row_block(0);
+  const double* Ac = uplo == 0 ? row_block(0) : row_block(n0);
+  const int64_t mr = uplo == 0 ? n1 : n0, nc = uplo == 0 ? n0 : n1;
+  double* Cb = uplo == 0 ? C + n0 * ldc : C + n0;
+  op.ta = trans;
+  op.tb = 1 - trans;
+  const strassen_variant v = levels == -1 ? STRASSEN_AUTO : STRASSEN_ABC;
+  return run_product(mr, nc, k, Ar, lda, Ac, lda, Cb, ldc, levels, v, STRASSEN_F64, s, op);
+}
+
 }  // namespace
 
 extern "C" {
+
+int strassen_dsyrk(int uplo, int trans, int64_t n, int64_t k, double alpha, const double* A, int64_t lda, double beta,
+                   double* C, int64_t ldc, int levels, unsigned flags, strassen_stream_t stream) {
+  try {
+    if (uplo < 0 || uplo > 1 || trans < 0 || trans > 1) return STRASSEN_ERR_ARG;
+    if (flags & ~(unsigned)STRASSEN_FLAG_DETERMINISTIC) return STRASSEN_ERR_ARG;
+    if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
+    if (n < 0 || k < 0) return STRASSEN_ERR_DIM;
+    if (n == 0) return STRASSEN_OK;
+    if (!C) return STRASSEN_ERR_NULL;
+    if (ldc < n) return STRASSEN_ERR_LD;
+    const bool product = k > 0 && alpha != 0.0;
+    if (product) {
+      if (!A) return STRASSEN_ERR_NULL;
+      const int64_t ar = trans ? k : n, ac = trans ? n : k;
+      if (lda < ac) return STRASSEN_ERR_LD;
+      const char* a0 = (const char*)A;
+      const char* a1 = (const char*)(A + (ar - 1) * lda + ac);
+      const char* c0 = (const char*)C;
+      const char* c1 = (const char*)(C + (n - 1) * ldc + n);
+      if (c0 < a1 && a0 < c1) return STRASSEN_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      return STRASSEN_ERR_CUDA;
+    }
+    // C = beta C on the triangle (beta = 0 writes zeros), then the products with beta 1.
+    if (launch_scale(C, ldc, n, n, beta, s, uplo == 0 ? 1 : 2) != cudaSuccess) return STRASSEN_ERR_CUDA;
+    if (!product) return STRASSEN_OK;
+    return run_syrk(uplo, trans, n, k, alpha, A, lda, C, ldc, levels, s, (flags & STRASSEN_FLAG_DETERMINISTIC) ? 1 : 0);
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
+}
+
 
 int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                   int64_t ldb, double* C, int64_t ldc, int levels, strassen_variant variant,
@@ -302,6 +425,10 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
       const strassen_problem& p = probs[i];
       if (p.levels < -1 || p.levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
       if ((int)p.variant < 0 || (int)p.variant > 3) return STRASSEN_ERR_UNSUPPORTED;
+      // The persistent launch runs the fused (ABC) form only: AB and Naive need their
+      // temporaries and separate passes per product.
+      if ((p.variant == STRASSEN_AB || p.variant == STRASSEN_NAIVE) && p.levels != 0)
+        return STRASSEN_ERR_UNSUPPORTED;
       const int chk = check_args(p.m, p.n, p.k, p.A, p.lda, p.B, p.ldb, p.C, p.ldc);
       if (chk < 0) return chk;
       if (chk == 1) continue;
@@ -347,26 +474,65 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
       cudaGetLastError();
       return STRASSEN_ERR_CUDA;
     }
+    // One persistent launch per (tile, levels) group -- the kernel instance fits the
+    // group's term count and tile -- issued largest first, alternately on the caller's
+    // stream and a library side stream forked from it, so that each launch's tail
+    // overlaps the next launch's start; the caller's stream waits for both at the end.
+    std::stable_sort(launches.begin(), launches.end(), [](const Fp64Launch& a, const Fp64Launch& b) {
+      return a.tile != b.tile ? a.tile < b.tile : a.levels < b.levels;
+    });
+    struct Group {
+      size_t begin, end;
+      double work;
+    };
+    std::vector<Group> groups;
+    size_t scratch_bytes = 0;
+    for (size_t i = 0; i < launches.size();) {
+      size_t j = i;
+      double w = 0.0;
+      while (j < launches.size() && launches[j].tile == launches[i].tile && launches[j].levels == launches[i].levels) {
+        w += fp64_launch_estimate(launches[j], launches[j].tile, 1);
+        ++j;
+      }
+      groups.push_back(Group{i, j, w});
+      scratch_bytes += (fp64_batched_scratch_bytes((int)(j - i)) + 255) / 256 * 256;
+      i = j;
+    }
+    std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.work > b.work; });
     Workspace ws;
     ws.s = s;
-    if (cudaMallocAsync(&ws.p, 2 * fp64_batched_scratch_bytes((int)launches.size()), s) != cudaSuccess) {
+    if (cudaMallocAsync(&ws.p, scratch_bytes, s) != cudaSuccess) {
       cudaGetLastError();
       ws.p = nullptr;
       return STRASSEN_ERR_ALLOC;
     }
-    std::stable_partition(launches.begin(), launches.end(), [](const Fp64Launch& L) { return L.tile == 0; });
-    const size_t n0 = (size_t)std::count_if(launches.begin(), launches.end(),
-                                            [](const Fp64Launch& L) { return L.tile == 0; });
-    if (n0 > 0) {
-      const cudaError_t e = launch_fp64_batched(launches.data(), (int)n0, ws.p, s);
-      if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (groups.size() > 1) {
+      if (side_stream(&side) != cudaSuccess || cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(side, fork, 0) != cudaSuccess) {
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        return STRASSEN_ERR_CUDA;
+      }
     }
-    if (n0 < launches.size()) {
-      void* scratch1 = (char*)ws.p + fp64_batched_scratch_bytes((int)n0);
-      const cudaError_t e = launch_fp64_batched(launches.data() + n0, (int)(launches.size() - n0), scratch1, s);
-      if (e != cudaSuccess) return STRASSEN_ERR_CUDA;
+    int st = STRASSEN_OK;
+    char* scratch = (char*)ws.p;
+    for (size_t g = 0; g < groups.size() && st == STRASSEN_OK; ++g) {
+      const int cnt = (int)(groups[g].end - groups[g].begin);
+      cudaStream_t gs = (g % 2 == 0) ? s : side;
+      if (launch_fp64_batched(launches.data() + groups[g].begin, cnt, scratch, gs) != cudaSuccess)
+        st = STRASSEN_ERR_CUDA;
+      scratch += (fp64_batched_scratch_bytes(cnt) + 255) / 256 * 256;
     }
-    return STRASSEN_OK;
+    if (side) {
+      if (cudaEventRecord(join, side) != cudaSuccess || cudaStreamWaitEvent(s, join, 0) != cudaSuccess)
+        st = STRASSEN_ERR_CUDA;
+      cudaEventDestroy(fork);
+      cudaEventDestroy(join);
+    }
+    return st;
   } catch (...) {
     return STRASSEN_ERR_ALLOC;
   }
@@ -436,37 +602,11 @@ int strassen_select(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, int* 
   if (!levels || !variant || !tile_id) return STRASSEN_ERR_NULL;
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
-  int lv = 0, var = STRASSEN_ABC, tile = 0;
-  int cand = -1;
-  if (record_lookup(m, n, k, (int)dtype, &lv, &var, &tile)) {
-    // exhaustive measurement
-  } else if (m > 0 && n > 0 && k > 0 && mlp_select(m, n, k, (int)dtype, &cand)) {
-    static const int kLv[7] = {0, 1, 1, 1, 2, 2, 2};
-    static const int kVar[7] = {STRASSEN_ABC, STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE,
-                                STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE};
-    lv = kLv[cand];
-    var = kVar[cand];
-    // the network picks levels and variant; the tile follows the analytic model
-    tile = 0;
-    if (dtype == STRASSEN_F64) {
-      double best = 1e300;
-      for (int t = 0; t < kNumTiles; ++t) {
-        const double x = model_seconds(m, n, k, lv, var, t);
-        if (x < best) { best = x; tile = t; }
-      }
-    }
-  } else {
-    if (dtype == STRASSEN_F64) {
-      model_select(m, n, k, &lv, &var, &tile);
-    } else {  // split precision: tensor-core products, no FP64 model; classical slices
-      lv = 0;
-      var = STRASSEN_ABC;
-      tile = 0;
-    }
+  try {
+    select_plan(m, n, k, (int)dtype, 1, levels, variant, tile_id);
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
   }
-  *levels = lv;
-  *variant = (strassen_variant)var;
-  *tile_id = tile;
   return STRASSEN_OK;
 }
 

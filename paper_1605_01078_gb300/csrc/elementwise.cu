@@ -71,11 +71,12 @@ __global__ void combine_kernel(const __grid_constant__ CombineParams p) {
 
 // C = beta C over the m x n operand (BLAS semantics: beta = 0 writes zeros without
 // reading C).
-__global__ void scale_kernel(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta) {
+__global__ void scale_kernel(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta, int tri) {
   const int64_t total = rows * cols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / cols, j = e - (e / cols) * cols;
+    if ((tri == 1 && j > i) || (tri == 2 && j < i)) continue;
     double* d = C + i * ldc + j;
     *d = beta == 0.0 ? 0.0 : beta * *d;
   }
@@ -119,10 +120,11 @@ cudaError_t launch_combine(double* C, int64_t ldc, int64_t c_rows, int64_t c_col
   return cudaGetLastError();
 }
 
-cudaError_t launch_scale(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta, cudaStream_t stream) {
+cudaError_t launch_scale(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta, cudaStream_t stream,
+                         int tri) {
   if (rows <= 0 || cols <= 0 || beta == 1.0) return cudaSuccess;
   const int threads = 256;
-  scale_kernel<<<grid_for(rows * cols, threads), threads, 0, stream>>>(C, ldc, rows, cols, beta);
+  scale_kernel<<<grid_for(rows * cols, threads), threads, 0, stream>>>(C, ldc, rows, cols, beta, tri);
   return cudaGetLastError();
 }
 

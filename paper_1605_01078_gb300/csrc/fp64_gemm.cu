@@ -24,7 +24,8 @@
 //       length of that sequence, set the error of the large products (about 2.4e-12
 //       of max|A| max|B| at 16384^3 with two levels, measured).  Chunks start from zero
 //       and are added into C, which shortens every sequential sum to the chunk length
-//       plus the number of chunks.
+//       plus the number of chunks.  The two halves of the consumer warps flush half a
+//       chunk apart, so the chunk flushes overlap the other half's multiply-adds.
 //
 // C updates are device atomics (red.global.add.f64) for every schedule; a store into a
 // temporary is a clear followed by adds.  The two groups hand tiles over through
@@ -112,6 +113,7 @@ struct alignas(128) ProbDesc {
   int32_t use_tma;
   int32_t flush_steps;       // k-steps per accumulation chunk (partial sums leave the registers)
   int32_t trans_a, trans_b;  // op(A) = A^T (A stored k x m), op(B) = B^T (B stored n x k)
+  int32_t tri;               // level 0: 0 all of C, 1 only j <= i, 2 only j >= i (local to C)
   double alpha;              // the product is scaled by alpha in the scatter
 };
 
@@ -130,9 +132,9 @@ struct KArgs {
 // What the producers tell the consumers about the k-step in a summed slot.
 struct StepMeta {
   int p, r, t;  // problem, product, tile of the step
-  int flags;    // kStepLast: the step ends a partial sum (see cursor_last); kStepEnd: no step
+  int flags;    // kStepLast, kStepFlush0, kStepFlush1 (see step_flags); kStepEnd: no step
 };
-constexpr int kStepLast = 1, kStepEnd = 2;
+constexpr int kStepLast = 1, kStepEnd = 2, kStepFlush0 = 4, kStepFlush1 = 8;
 
 template <int MAXT, int BT>
 struct Smem {
@@ -269,13 +271,20 @@ __device__ Cursor range_cursor(const KArgs& a, int64_t id) {
   return c;
 }
 
-// True when the k-step ends a partial sum: the unit's last k-step, the end of this
-// block's share of a unit split by stream-K, or the end of an accumulation chunk.
+// Flags of a k-step: kStepLast when it ends this block's part of the unit (the unit's
+// last k-step, or the end of a stream-K share); kStepFlush0 / kStepFlush1 when it ends
+// an accumulation chunk of consumer group 0 / 1.  Both groups flush every flush_steps
+// k-steps, group 1 half a chunk later than group 0, so that while one group adds its
+// partial sums into C the other keeps the FP64 pipe busy.
 template <bool BATCHED>
-__device__ __forceinline__ bool cursor_last(const KArgs& a, const Cursor& c) {
+__device__ __forceinline__ int step_flags(const KArgs& a, const Cursor& c) {
   const ProbDesc& d = desc_of<BATCHED>(a, c.p);
-  return c.ks == d.ksteps - 1 || (c.ks + 1) % d.flush_steps == 0 ||
-         ((BATCHED || a.sched == kSchedStreamK) && c.left == 1);
+  int f = 0;
+  if (c.ks == d.ksteps - 1 || ((BATCHED || a.sched == kSchedStreamK) && c.left == 1)) f |= kStepLast;
+  const int kk = c.ks + 1, fs = d.flush_steps;
+  if (kk % fs == 0) f |= kStepFlush0;
+  if ((kk + fs / 2) % fs == 0) f |= kStepFlush1;
+  return f;
 }
 
 template <bool BATCHED>
@@ -573,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 #pragma unroll
         for (int i = 0; i < EPT; ++i) sb[(koff + i) * BN + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
       }
-      if (pt == 0) meta[q] = StepMeta{cur.p, cur.r, cur.t, cursor_last<BATCHED>(a, cur) ? kStepLast : 0};
+      if (pt == 0) meta[q] = StepMeta{cur.p, cur.r, cur.t, step_flags<BATCHED>(a, cur)};
       mbar_arrive(&sum_full[q]);
       mbar_arrive(&raw_empty[slot]);
       cursor_next<BATCHED>(a, cur);
@@ -600,6 +609,10 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
   // ======================= consumers =======================
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kConsumerRegs));
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  // Consumer group of the accumulation chunks: warps 0-3 and 4-7 (warps w and w + 4
+  // share an SM sub-partition, so each sub-partition keeps one computing warp while
+  // the other flushes).
+  const int flush_bit = (tid >> 5) < 4 ? kStepFlush0 : kStepFlush1;
   double acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -646,7 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
     const StepMeta m = meta[q];
     mbar_arrive(&sum_empty[q]);
 
-    if (m.flags & kStepLast) {
+    if (m.flags & (kStepLast | flush_bit)) {
       // Scatter epilogue: C_q += gamma_q * M_tile for every target of the product.
       // The tile leaves the registers one row group at a time through a per-warp
       // staging buffer, so that each warp issues coalesced atomics over whole tile rows
@@ -685,7 +698,9 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
             const int e = lane + 32 * q;
             const int h = e / BN, col = e - (e / BN) * BN;
             const int rr = h ? rr1 : rr0;
-            if (rr < row_lim && col < col_lim)
+            const int64_t gi = row0 + rr, gj = col0 + col;
+            const bool in_tri = d.tri == 0 || (d.tri == 1 ? gj <= gi : gj >= gi);
+            if (rr < row_lim && col < col_lim && in_tri)
               // red.global.add.f64, performed in the L2 (off the FP64 pipe).  Each C
               // element of a tile is always updated by the same thread, in product
               // order, so one owner per tile gives a deterministic result.
@@ -822,6 +837,7 @@ void fill_desc(const Fp64Launch& L, ProbDesc* d) {
   d->ksteps = (int)((L.hk + BK - 1) / BK);
   d->trans_a = L.trans_a;
   d->trans_b = L.trans_b;
+  d->tri = L.levels == 0 ? L.tri : 0;
   d->alpha = L.alpha;
   d->flush_steps = accumulation_chunk_k(L.levels) / BK;
   // The innermost TMA coordinate is a block offset along k (A), n (B), m (A^T) or k

@@ -63,6 +63,7 @@ struct Fp64Launch {
   int tile;                // 0: 128 x 128 block tile, 1: 64 x 64, -1: the library's choice
   int trans_a, trans_b;    // op(A) = A^T (A stored k x m, ld >= m); op(B) = B^T (stored n x k)
   double alpha;            // C += alpha * (product); 1 for the plain operation
+  int tri;                 // level 0 only: 0 every element of C, 1 only j <= i, 2 only j >= i
 };
 
 // Fills the fields common to a full-operand launch.
@@ -128,7 +129,9 @@ cudaError_t launch_combine(double* C, int64_t ldc, int64_t c_rows, int64_t c_col
                            const double* M, int64_t hm, int64_t hn,
                            const uint8_t* targets, int ntargets, cudaStream_t stream, double alpha = 1.0);
 // C (rows x cols, ldc) = beta C; beta = 0 writes zeros without reading C; beta = 1 is a no-op.
-cudaError_t launch_scale(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta, cudaStream_t stream);
+// With tri = 1 (2) only the elements with j <= i (j >= i) are scaled.
+cudaError_t launch_scale(double* C, int64_t ldc, int64_t rows, int64_t cols, double beta, cudaStream_t stream,
+                         int tri = 0);
 
 int device_sm_count();
 
@@ -142,14 +145,27 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                       double* C, int64_t ldc, int levels, void* ws, cudaStream_t stream, int trans_a = 0,
                       int trans_b = 0, double alpha = 1.0, cudaEvent_t* stage_events = nullptr);
 int ozaki_device_status();
+// Analytic time of a split-precision call (the selector's model for that dtype).
+double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels);
 
-// Learned selector (mlp.cu): argmin of the loaded MLP's predictions for a shape;
-// false when no network is loaded (or it lives on another device).  Candidate c maps
-// to (levels, variant): 0 (0,ABC) 1 (1,ABC) 2 (1,AB) 3 (1,Naive) 4 (2,ABC) 5 (2,AB) 6 (2,Naive).
-bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate);
+// Learned selector (mlp.cu).  Candidates: c = 0, 1 classical with tile c; c = 2 + 6 (L - 1)
+// + 2 v + t: L levels (1..3) of variant v (ABC, AB, Naive) with tile t.  The split-precision
+// dtype takes the tile-0 ABC candidates only (levels 0..3).
+constexpr int kSelCandidates = 2 + 6 * kMaxLevels;
+constexpr int kSelInputs = 6 + kSelCandidates;
+void selector_candidate(int c, int* levels, int* variant, int* tile);
+bool selector_candidate_valid(int c, int dtype);
+// Network inputs x[kSelInputs] and the analytic model's log2 seconds base[kSelCandidates].
+void selector_features(int64_t m, int64_t n, int64_t k, int dtype, float* x, float* base);
+// Argmin over the valid candidates of base + the loaded MLP's correction, for a shape;
+// false when no network is loaded or enabled for the dtype, it lives on another device,
+// or `may_launch` is 0 and the shape's choice is not cached (the first choice for a
+// shape launches the select kernel and waits for it; later ones come from a host cache).
+bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int may_launch, int* candidate);
 
 // Selection (select.cpp): analytic time model, its argmin, and the exhaustive records.
 double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant, int tile);
+double model_seconds_dtype(int64_t m, int64_t n, int64_t k, int levels, int variant, int tile, int dtype);
 void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant, int* tile);
 bool record_lookup(int64_t m, int64_t n, int64_t k, int dtype, int* levels, int* variant, int* tile);
 void record_store(int64_t m, int64_t n, int64_t k, int dtype, int levels, int variant, int tile);

@@ -1,26 +1,32 @@
-// Learned variant selector: a small MLP (6 -> 64 -> 64 -> 7, FP32, ReLU) that predicts
-// the log2 run time of each member of the family -- classical, and 1 / 2 levels of ABC,
-// AB and Naive -- from log2 m, log2 n, log2 k and the dtype.  It stands in for the
-// analytic performance model of Section 4.2 when choosing the implementation.
+// Learned variant selector: a small MLP (26 -> 64 -> 64 -> 20, FP32, ReLU) that
+// predicts, for each of 20 candidates -- classical, and 1, 2 or 3 levels of ABC, AB and
+// Naive, each with the 128x128 or the 64x64 block tile -- the log2 run time of a shape
+// as a correction to the analytic performance model's prediction.  Its inputs are
+// log2 m, log2 n, log2 k, the dtype and the model's log2 seconds for every candidate
+// (which carry the padding of each tile, invisible in the sizes alone).  It stands in
+// for the analytic model of Section 4.2 when choosing the implementation: the choice is
+// the argmin of model + correction.
 //
 // Hand-written kernels: forward, loss gradient (forward + reverse mode per sample,
 // per-block gradient sums in shared memory, one atomic add per parameter per block),
 // Adam, and the single-shape selection used by strassen_select().
 //
-// Parameter vector (float): [W1 (64x6, row-major), b1 (64), W2 (64x64), b2 (64),
-// W3 (7x64), b3 (7)].  Loss: masked mean squared error over measured candidates.
+// Parameter vector (float): [W1 (64x26, row-major), b1 (64), W2 (64x64), b2 (64),
+// W3 (20x64), b3 (20)].  Loss: masked mean squared error over measured candidates of
+// (network output - (log2 measured seconds - model log2 seconds)).
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 
 #include "internal.h"
 
 namespace sgb {
 namespace {
 
-constexpr int kIn = 6, kH = 64, kOut = 7;
+constexpr int kIn = kSelInputs, kH = 64, kOut = kSelCandidates;
 constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, oW3 = ob2 + kH,
               ob3 = oW3 + kOut * kH, kParams = ob3 + kOut;
 constexpr int kBlock = 64;  // one thread per hidden unit
@@ -122,7 +128,8 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 
 struct SelectArgs {
   float x[kIn];
-  unsigned valid;  // bit c set: candidate c may be chosen
+  float base[kOut];  // the analytic model's log2 seconds per candidate
+  unsigned valid;    // bit c set: candidate c may be chosen
 };
 
 __global__ void __launch_bounds__(kBlock) mlp_select_kernel(const float* __restrict__ params,
@@ -136,35 +143,93 @@ __global__ void __launch_bounds__(kBlock) mlp_select_kernel(const float* __restr
   sample_forward(P, x, z1, h1, z2, h2, y);
   if (threadIdx.x == 0) {
     int best = -1;
-    for (int c = 0; c < kOut; ++c)
-      if (((a.valid >> c) & 1u) && (best < 0 || y[c] < y[best])) best = c;
+    float bv = 0.f;
+    for (int c = 0; c < kOut; ++c) {
+      const float v = a.base[c] + y[c];
+      if (((a.valid >> c) & 1u) && (best < 0 || v < bv)) {
+        best = c;
+        bv = v;
+      }
+    }
     *out = best;
   }
 }
 
 // ---------------------------------------------------------------- selector state
 
+struct ShapeKey {
+  int64_t m, n, k;
+  int dtype;
+  bool operator==(const ShapeKey& o) const { return m == o.m && n == o.n && k == o.k && dtype == o.dtype; }
+};
+struct ShapeKeyHash {
+  size_t operator()(const ShapeKey& s) const {
+    uint64_t h = 1469598103934665603ull;
+    for (uint64_t v : {(uint64_t)s.m, (uint64_t)s.n, (uint64_t)s.k, (uint64_t)s.dtype}) {
+      h ^= v;
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+
 std::mutex g_mlp_mu;
-float* g_sel_params = nullptr;  // device copy of the loaded network (device 0 of the loader)
+float* g_sel_params = nullptr;  // device copy of the loaded network (on the loader's device)
 int* g_sel_out = nullptr;
 cudaStream_t g_sel_stream = nullptr;
 int g_sel_device = -1;
 unsigned g_sel_dtypes = 0x7u;  // bit d: use the network for dtype d
+std::unordered_map<ShapeKey, int, ShapeKeyHash> g_sel_cache;  // choices of the loaded network
 
 int grid_for_batch(int batch) { return batch < 1 ? 1 : (batch < 1024 ? batch : 1024); }
 
 }  // namespace
 
-void mlp_features(int64_t m, int64_t n, int64_t k, int dtype, float* x) {
+void selector_candidate(int c, int* levels, int* variant, int* tile) {
+  if (c < 2) {
+    *levels = 0;
+    *variant = STRASSEN_ABC;
+    *tile = c < 0 ? 0 : c;
+    return;
+  }
+  const int r = c - 2;
+  *levels = 1 + r / 6;
+  *variant = (r % 6) / 2;
+  *tile = r % 2;
+}
+
+bool selector_candidate_valid(int c, int dtype) {
+  if (c < 0 || c >= kOut) return false;
+  if (dtype == STRASSEN_F64) return true;
+  int lv, var, tile;
+  selector_candidate(c, &lv, &var, &tile);
+  return dtype == STRASSEN_F64_OZ_BF16 && var == STRASSEN_ABC && tile == 0;
+}
+
+void selector_features(int64_t m, int64_t n, int64_t k, int dtype, float* x, float* base) {
   x[0] = (float)((std::log2((double)m) - 11.0) / 3.0);
   x[1] = (float)((std::log2((double)n) - 11.0) / 3.0);
   x[2] = (float)((std::log2((double)k) - 11.0) / 3.0);
   x[3] = dtype == 0 ? 1.f : 0.f;
   x[4] = dtype == 1 ? 1.f : 0.f;
   x[5] = dtype == 2 ? 1.f : 0.f;
+  for (int c = 0; c < kOut; ++c) {
+    int lv, var, tile;
+    selector_candidate(c, &lv, &var, &tile);
+    // candidates that do not apply to the dtype carry the value of one that does
+    if (!selector_candidate_valid(c, dtype)) {
+      var = STRASSEN_ABC;
+      tile = 0;
+    }
+    const int64_t mn = std::min(m, std::min(n, k));
+    while (lv > 0 && ((int64_t)1 << lv) > mn) --lv;
+    const double t = model_seconds_dtype(m, n, k, lv, var, tile, dtype);
+    base[c] = (float)std::log2(t > 1e-9 ? t : 1e-9);
+    x[6 + c] = (base[c] + 7.f) / 7.f;
+  }
 }
 
-bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate) {
+bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int may_launch, int* candidate) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
   if (!g_sel_params || dtype < 0 || dtype > 2 || !((g_sel_dtypes >> dtype) & 1u)) return false;
   int dev = 0;
@@ -172,9 +237,18 @@ bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate) {
     cudaGetLastError();
     return false;
   }
+  const ShapeKey key{m, n, k, dtype};
+  auto it = g_sel_cache.find(key);
+  if (it != g_sel_cache.end()) {
+    *candidate = it->second;
+    return true;
+  }
+  if (!may_launch) return false;
   SelectArgs a;
-  mlp_features(m, n, k, dtype, a.x);
-  a.valid = dtype == STRASSEN_F64 ? 0x7Fu : 0x13u;  // split precision: levels 0, 1, 2 of ABC
+  selector_features(m, n, k, dtype, a.x, a.base);
+  a.valid = 0;
+  for (int c = 0; c < kOut; ++c)
+    if (selector_candidate_valid(c, dtype)) a.valid |= 1u << c;
   mlp_select_kernel<<<1, kBlock, 0, g_sel_stream>>>(g_sel_params, a, g_sel_out);
   int host = -1;
   if (cudaMemcpyAsync(&host, g_sel_out, sizeof(int), cudaMemcpyDeviceToHost, g_sel_stream) != cudaSuccess ||
@@ -183,6 +257,8 @@ bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int* candidate) {
     return false;
   }
   if (host < 0 || host >= kOut) return false;
+  if (g_sel_cache.size() > 100000) g_sel_cache.clear();
+  g_sel_cache[key] = host;
   *candidate = host;
   return true;
 }
@@ -243,6 +319,7 @@ int strassen_selector_load(const float* params_host, int count) {
   }
   if (cudaMemcpy(g_sel_params, params_host, sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess)
     return STRASSEN_ERR_CUDA;
+  g_sel_cache.clear();
   return STRASSEN_OK;
 }
 
@@ -251,6 +328,34 @@ int strassen_selector_use(int dtype, int enable) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
   if (enable) g_sel_dtypes |= 1u << dtype;
   else g_sel_dtypes &= ~(1u << dtype);
+  g_sel_cache.clear();
+  return STRASSEN_OK;
+}
+
+int strassen_selector_candidate(int candidate, int* levels, strassen_variant* variant, int* tile_id) {
+  if (!levels || !variant || !tile_id) return STRASSEN_ERR_NULL;
+  if (candidate < 0 || candidate >= kOut) return STRASSEN_ERR_ARG;
+  int lv, var, tile;
+  selector_candidate(candidate, &lv, &var, &tile);
+  *levels = lv;
+  *variant = (strassen_variant)var;
+  *tile_id = tile;
+  return STRASSEN_OK;
+}
+
+int strassen_selector_features(int64_t m, int64_t n, int64_t k, strassen_dtype dtype, float* x, float* base,
+                               unsigned* valid) {
+  if (!x || !base || !valid) return STRASSEN_ERR_NULL;
+  if (m <= 0 || n <= 0 || k <= 0) return STRASSEN_ERR_DIM;
+  if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
+  try {
+    selector_features(m, n, k, (int)dtype, x, base);
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
+  }
+  *valid = 0;
+  for (int c = 0; c < kOut; ++c)
+    if (selector_candidate_valid(c, (int)dtype)) *valid |= 1u << c;
   return STRASSEN_OK;
 }
 
@@ -267,6 +372,7 @@ int strassen_selector_clear(void) {
     g_sel_device = -1;
   }
   g_sel_dtypes = 0x7u;
+  g_sel_cache.clear();
   return STRASSEN_OK;
 }
 

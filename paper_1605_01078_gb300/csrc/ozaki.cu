@@ -757,6 +757,36 @@ int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
          4096;
 }
 
+double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels) {
+  if (m <= 0 || n <= 0 || k <= 0 || levels < 0 || levels > kMaxLevels) return 1e30;
+  const int sms = std::max(device_sm_count(), 1);
+  const int64_t P = kPlanCount[levels];
+  const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
+  const int64_t hmp = round_up(hm, kTM), hnp = round_up(hn, kTN), hkp = round_up(hk, kTK);
+  const int64_t nseg = plan_segments(P * (hmp / kTM) * (hnp / kTN), hkp / kTK, sms);
+  int64_t ta = 0, tb = 0, tc = 0;
+  for (int r = 0; r < P; ++r) {
+    const int row = kPlanOffset[levels] + r;
+    ta += kPlanTables.na[row];
+    tb += kPlanTables.nb[row];
+    tc += kPlanTables.nc[row];
+  }
+  int pairs = 0;
+  for (int w = 2; w <= kS + 1; ++w) pairs += pairs_of(w);
+  // Slice products at the tensor rate the kernel reaches on large shapes (0.8 of the
+  // BF16 dense peak of about 12.7K flops per clock per SM at 2 GHz), in whole waves.
+  const double units = (double)P * (hmp / kTM) * (hnp / kTN) * nseg;
+  const double waves = std::ceil(units / sms);
+  const double unit_flops = (double)pairs * 2.0 * kTM * kTN * ((double)hkp / nseg);
+  const double t_mma = waves * unit_flops / (0.8 * 12700.0 * 2.0e9);
+  // HBM passes: operand reads per term (B twice: column maxima, then digits), digit
+  // writes and reads, group-sum writes and reads, C read and write.
+  const double bytes = 8.0 * (ta * hm * hk + 2.0 * tb * hk * hn) + 2.0 * 2.0 * kS * P * (hmp + hnp) * hkp +
+                       2.0 * 4.0 * nseg * kGroups * P * hmp * hnp + 4.0 * kGroups * nseg * (double)tc * hm * hn +
+                       16.0 * m * n;
+  return t_mma + bytes / 6.8e12 + 5 * 4e-6;
+}
+
 int ozaki_device_status() {
   int v = 0;
   if (cudaMemcpyFromSymbol(&v, g_oz_status, sizeof(int)) != cudaSuccess) return STRASSEN_ERR_CUDA;

@@ -4,8 +4,9 @@
 //
 // Order of precedence in strassen_select():
 //   1. an exhaustive-measurement record for the exact shape (strassen_tune_record);
-//   2. the learned selector (an MLP over log2 m, log2 n, log2 k and the dtype), when
-//      one is loaded (strassen_selector_load);
+//   2. the learned selector (an MLP over log2 m, log2 n, log2 k, the dtype and this
+//      model's prediction for every candidate, which it corrects), when one is loaded
+//      (strassen_selector_load) and enabled for the dtype;
 //   3. the analytic model below.
 //
 // The analytic model restates the paper's T = T_a + T_m for this GPU: T_a counts the
@@ -14,7 +15,9 @@
 // additions of Naive and AB's separate kernels (the staging sums of ABC and AB run on
 // the integer pipe and cost no FP64 time) -- at the FP64 pipe rate; T_m counts the extra
 // passes of AB and Naive over their temporaries at the HBM rate; and each kernel launch
-// costs a fixed overhead.
+// costs a fixed overhead.  The FP64 rate comes from the device's SM count and clock.
+// For the split-precision dtype the model is ozaki_model_seconds (tensor-core slice
+// products plus the HBM passes of the splits and the recombination).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,7 +30,7 @@
 namespace sgb {
 namespace {
 
-constexpr double kFmaPerSec = 2.0 * 152 * 2.07e9;   // FP64 pipe: 2 FMA / clk / SM
+constexpr double kFmaPerClkPerSm = 2.0;             // FP64 pipe: 2 FMA / clk / SM (measured)
 constexpr double kAddCost = 1.2;                    // a DADD costs about 1.2 DFMA (measured)
 constexpr double kStageAddCost = 0.0;               // staging sums run on the integer pipe
 constexpr double kBytesPerSec = 6.8e12;             // HBM, measured copy bandwidth
@@ -57,6 +60,30 @@ struct Choice {
 
 std::mutex g_sel_mu;
 std::unordered_map<Key, Choice, KeyHash> g_records;
+
+// FP64 multiply-adds per second of the current device: SM count and peak SM clock
+// from the device attributes (cached per device; GB300 values when no device answers).
+double fma_per_sec() {
+  static std::mutex mu;
+  static double cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return kFmaPerClkPerSm * 152 * 2.07e9;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache[dev] == 0.0) {
+    int sms = 0, khz = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || sms <= 0 || khz <= 0) {
+      cudaGetLastError();
+      sms = 152;
+      khz = 2070000;
+    }
+    cache[dev] = kFmaPerClkPerSm * sms * (khz * 1e3);
+  }
+  return cache[dev];
+}
 
 }  // namespace
 
@@ -97,7 +124,12 @@ double model_seconds(int64_t m, int64_t n, int64_t k, int levels, int variant, i
     }
     launches = 5.0 * pl.nprod;
   }
-  return (tile_factor * fma + kAddCost * adds) / kFmaPerSec + bytes / kBytesPerSec + launches * kLaunchSec;
+  return (tile_factor * fma + kAddCost * adds) / fma_per_sec() + bytes / kBytesPerSec + launches * kLaunchSec;
+}
+
+double model_seconds_dtype(int64_t m, int64_t n, int64_t k, int levels, int variant, int tile, int dtype) {
+  if (dtype == STRASSEN_F64_OZ_BF16) return ozaki_model_seconds(m, n, k, levels);
+  return model_seconds(m, n, k, levels, variant, tile);
 }
 
 void model_select(int64_t m, int64_t n, int64_t k, int* levels, int* variant, int* tile) {

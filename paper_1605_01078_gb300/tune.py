@@ -24,23 +24,30 @@ import numpy as np
 
 from . import _binding as B
 
-# Candidate c -> (levels, variant), the order of the network's outputs.
-CANDIDATES: List[Tuple[int, int]] = [(0, B.STRASSEN_ABC), (1, B.STRASSEN_ABC), (1, B.STRASSEN_AB),
-                                     (1, B.STRASSEN_NAIVE), (2, B.STRASSEN_ABC), (2, B.STRASSEN_AB),
-                                     (2, B.STRASSEN_NAIVE)]
-VALID = {B.STRASSEN_F64: [0, 1, 2, 3, 4, 5, 6], B.STRASSEN_F64_OZ_BF16: [0, 1, 4]}
+NC = B.SELECTOR_CANDIDATES  # the network's outputs: candidate c -> (levels, variant, tile)
+
+
+def candidates() -> List[Tuple[int, int, int]]:
+    return [B.strassen_selector_candidate(c) for c in range(NC)]
+
+
+def valid_candidates(dtype: int) -> List[int]:
+    _, _, mask = B.strassen_selector_features(1024, 1024, 1024, dtype)
+    return [c for c in range(NC) if (mask >> c) & 1]
+
+
 DTYPE_NAME = {B.STRASSEN_F64: "f64", B.STRASSEN_F64_OZ_BF16: "oz_bf16"}
 
 
-def features(m, n, k, dtype) -> np.ndarray:
-    """Network inputs (float32): (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, one-hot dtype."""
-    m, n, k, dtype = (np.atleast_1d(np.asarray(v)) for v in (m, n, k, dtype))
-    x = np.zeros((m.size, 6), dtype=np.float32)
-    x[:, 0] = (np.log2(m) - 11.0) / 3.0
-    x[:, 1] = (np.log2(n) - 11.0) / 3.0
-    x[:, 2] = (np.log2(k) - 11.0) / 3.0
-    x[np.arange(m.size), 3 + dtype.astype(int)] = 1.0
-    return x
+def features(rows) -> Tuple[np.ndarray, np.ndarray]:
+    """Network inputs X [rows, 26] and the analytic model's log2 seconds [rows, 20], as
+    the library computes them (strassen_selector_features)."""
+    X = np.zeros((len(rows), B.SELECTOR_INPUTS), dtype=np.float32)
+    base = np.zeros((len(rows), NC), dtype=np.float32)
+    for i, r in enumerate(rows):
+        x, b, _ = B.strassen_selector_features(r["m"], r["n"], r["k"], r["dtype"])
+        X[i], base[i] = x, b
+    return X, base
 
 
 class Timer:
@@ -56,37 +63,55 @@ class Timer:
         self.e0 = torch.cuda.Event(enable_timing=True)
         self.e1 = torch.cuda.Event(enable_timing=True)
 
-    def _call(self, m, n, k, levels, variant, dtype):
+    def _call(self, m, n, k, dtype):
         st = B.strassen_gemm(m, n, k, self.A.data_ptr(), k, self.B.data_ptr(), n, self.C.data_ptr(), n,
-                             levels, variant, dtype, self.stream.cuda_stream)
+                             -1, B.STRASSEN_AUTO, dtype, self.stream.cuda_stream)
         if st != 0:
             raise B.StrassenError(st, "strassen_gemm")
 
-    def time(self, m, n, k, levels, variant, dtype, min_seconds=2e-3, max_reps=20) -> float:
-        """Median-free best-effort time: one untimed call, then repeated timed calls until
-        min_seconds of work (or max_reps); returns seconds per call."""
-        self._call(m, n, k, levels, variant, dtype)
-        reps, total = 0, 0.0
-        while reps < max_reps and (total < min_seconds or reps == 0):
+    def time(self, m, n, k, levels, variant, tile, dtype, min_seconds=2e-3, max_reps=20,
+             single_above=0.02) -> float:
+        """Seconds per call of exactly (levels, variant, tile) -- fixed by an exhaustive
+        record for the shape, which the automatic call follows.  A first call of at least
+        `single_above` seconds is the measurement; shorter ones are repeated (the first
+        discarded) until `min_seconds` of work or `max_reps` calls."""
+        st = B.strassen_tune_record(m, n, k, dtype, levels, variant, tile)
+        if st != 0:
+            raise B.StrassenError(st, "strassen_tune_record")
+        try:
             self.e0.record(self.stream)
-            self._call(m, n, k, levels, variant, dtype)
+            self._call(m, n, k, dtype)
             self.e1.record(self.stream)
             self.e1.synchronize()
-            total += self.e0.elapsed_time(self.e1) / 1e3
-            reps += 1
-        return total / reps
+            first = self.e0.elapsed_time(self.e1) / 1e3
+            if first >= single_above:
+                return first
+            reps, total = 0, 0.0
+            while reps < max_reps and (total < min_seconds or reps == 0):
+                self.e0.record(self.stream)
+                self._call(m, n, k, dtype)
+                self.e1.record(self.stream)
+                self.e1.synchronize()
+                total += self.e0.elapsed_time(self.e1) / 1e3
+                reps += 1
+            return total / reps
+        finally:
+            B.strassen_tune_clear()
 
 
 def measure(shapes: Sequence[Tuple[int, int, int]], dtype: int, timer: Timer,
-            candidates: Optional[Sequence[int]] = None) -> List[Dict]:
-    """Exhaustive timing: one row per shape with the seconds of every valid candidate."""
-    cands = list(VALID[dtype] if candidates is None else candidates)
+            cands: Optional[Sequence[int]] = None) -> List[Dict]:
+    """Exhaustive timing: one row per shape with the seconds of every valid candidate
+    (NaN for the others).  Candidates whose levels would be clamped for the shape are
+    timed as what they run."""
+    cl = candidates()
+    cs = list(valid_candidates(dtype) if cands is None else cands)
     rows = []
     for (m, n, k) in shapes:
-        times = [math.nan] * len(CANDIDATES)
-        for c in cands:
-            lv, var = CANDIDATES[c]
-            times[c] = timer.time(m, n, k, lv, var, dtype)
+        times = [math.nan] * NC
+        for c in cs:
+            lv, var, tile = cl[c]
+            times[c] = timer.time(m, n, k, lv, var, tile, dtype)
         rows.append({"m": int(m), "n": int(n), "k": int(k), "dtype": int(dtype), "times": times})
     return rows
 
@@ -98,34 +123,39 @@ def best_of(row) -> int:
 
 def record(rows) -> None:
     """Hand the exhaustive winners to the library's selection table."""
+    cl = candidates()
     for r in rows:
-        lv, var = CANDIDATES[best_of(r)]
-        st = B.strassen_tune_record(r["m"], r["n"], r["k"], r["dtype"], lv, var, 0)
+        lv, var, tile = cl[best_of(r)]
+        st = B.strassen_tune_record(r["m"], r["n"], r["k"], r["dtype"], lv, var, tile)
         if st != 0:
             raise B.StrassenError(st, "strassen_tune_record")
 
 
 def arrays(rows):
-    """Network inputs X, targets T = log2 seconds, and the mask of measured candidates."""
-    X = features([r["m"] for r in rows], [r["n"] for r in rows], [r["k"] for r in rows],
-                 [r["dtype"] for r in rows])
-    t = np.array([r["times"] for r in rows], dtype=np.float64)
-    mask = np.isfinite(t).astype(np.float32)
-    T = np.where(np.isfinite(t), np.log2(np.where(np.isfinite(t), t, 1.0)), 0.0).astype(np.float32)
-    return X, T, mask
+    """Network inputs X, targets T = log2 measured seconds - the model's log2 seconds
+    (the correction the network learns), the mask of measured candidates, and the
+    model's log2 seconds."""
+    X, base = features(rows)
+    t = np.array([r["times"] + [math.nan] * (NC - len(r["times"])) for r in rows], dtype=np.float64)
+    ok = np.isfinite(t)
+    mask = ok.astype(np.float32)
+    T = np.where(ok, np.log2(np.where(ok, t, 1.0)) - base, 0.0).astype(np.float32)
+    return X, T, mask, base
 
 
 def init_params(seed: int) -> np.ndarray:
-    """He-uniform weights, zero biases (float32), in the library's parameter order."""
+    """He-uniform weights for the hidden layers, zero output layer (float32), in the
+    library's parameter order: the untrained network predicts no correction, i.e. it
+    starts as the analytic model."""
     g = np.random.Generator(np.random.Philox(seed))
-    shapes = [(64, 6), (64,), (64, 64), (64,), (7, 64), (7,)]
+    shapes = [(64, B.SELECTOR_INPUTS), (64,), (64, 64), (64,), (NC, 64), (NC,)]
     parts = []
-    for shp in shapes:
-        if len(shp) == 2:
+    for i, shp in enumerate(shapes):
+        if len(shp) == 2 and i < 4:
             lim = math.sqrt(6.0 / shp[1])
             parts.append(g.uniform(-lim, lim, size=shp).ravel())
         else:
-            parts.append(np.zeros(shp))
+            parts.append(np.zeros(shp).ravel())
     return np.concatenate(parts).astype(np.float32)
 
 
@@ -134,7 +164,7 @@ def train(rows, steps: int = 3000, lr: float = 3e-3, seed: int = 0, params: Opti
     kernels.  Returns (parameters as numpy float32, loss history: step 0, then every
     100 steps)."""
     import torch
-    X, T, mask = arrays(rows)
+    X, T, mask, _ = arrays(rows)
     n_par = B.strassen_mlp_param_count()
     p0 = init_params(seed) if params is None else np.asarray(params, dtype=np.float32)
     assert p0.size == n_par
@@ -144,7 +174,7 @@ def train(rows, steps: int = 3000, lr: float = 3e-3, seed: int = 0, params: Opti
     G = torch.zeros_like(P)
     Mo = torch.zeros_like(P)
     V = torch.zeros_like(P)
-    Y = torch.empty((len(rows), 7), dtype=torch.float32, device="cuda")
+    Y = torch.empty((len(rows), NC), dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream().cuda_stream
     msum = float(mask.sum())
     hist = []
@@ -168,46 +198,55 @@ def train(rows, steps: int = 3000, lr: float = 3e-3, seed: int = 0, params: Opti
 
 
 def predict(params: np.ndarray, rows) -> np.ndarray:
-    """Predicted log2 seconds [rows, 7] from the library's forward kernel."""
+    """Predicted log2 seconds [rows, 20]: the model's plus the network's correction (the
+    library's forward kernel)."""
     import torch
-    X, _, _ = arrays(rows)
+    X, _, _, base = arrays(rows)
     P = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
     dX = torch.from_numpy(X).cuda()
-    Y = torch.empty((len(rows), 7), dtype=torch.float32, device="cuda")
+    Y = torch.empty((len(rows), NC), dtype=torch.float32, device="cuda")
     st = B.strassen_mlp_forward(P.data_ptr(), dX.data_ptr(), len(rows), Y.data_ptr(),
                                 torch.cuda.current_stream().cuda_stream)
     if st != 0:
         raise B.StrassenError(st, "strassen_mlp_forward")
-    return Y.cpu().numpy()
+    return Y.cpu().numpy() + base
 
 
 def choose_mlp(params, rows) -> List[int]:
     Y = predict(params, rows)
     out = []
     for r, y in zip(rows, Y):
-        valid = VALID[r["dtype"]]
+        valid = valid_candidates(r["dtype"])
         out.append(int(valid[int(np.argmin(y[valid]))]))
     return out
 
 
 def choose_model(rows) -> List[int]:
-    """Argmin of the analytic model (FP64 candidates); split precision: classical."""
+    """The selection without the network: the analytic model's choice for FP64 (its own
+    argmin with the 1 % tie-break, as strassen_select returns it), classical slices for
+    split precision."""
+    cl = candidates()
     out = []
-    for r in rows:
-        if r["dtype"] != B.STRASSEN_F64:
-            out.append(0)
-            continue
-        t = [B.strassen_model_seconds(r["m"], r["n"], r["k"], lv, var) for (lv, var) in CANDIDATES]
-        out.append(int(np.argmin(t)))
+    B.strassen_selector_use(B.STRASSEN_F64, 0)  # a loaded network must not answer here
+    try:
+        for r in rows:
+            if r["dtype"] != B.STRASSEN_F64:
+                out.append(0)
+                continue
+            out.append(cl.index(B.strassen_select(r["m"], r["n"], r["k"], r["dtype"])))
+    finally:
+        B.strassen_selector_use(B.STRASSEN_F64, 1)
     return out
 
 
 def choose_fixed(rows, candidate: int) -> List[int]:
-    return [candidate if candidate in VALID[r["dtype"]] else 0 for r in rows]
+    return [candidate if candidate in valid_candidates(r["dtype"]) else 0 for r in rows]
 
 
 def regret(rows, choices) -> Dict[str, float]:
     """Mean and 95th percentile of t(chosen)/t(best) - 1 over the rows."""
+    if not rows:
+        return {"mean": None, "p95": None, "max": None, "n": 0}
     reg = []
     for r, c in zip(rows, choices):
         t = np.array(r["times"], dtype=np.float64)
@@ -252,27 +291,30 @@ def load_rows(path: str):
 
 SWEEP_SQUARE = [2048 * i for i in range(1, 9)]
 SWEEP_RANKK = [256, 512, 1024, 2048, 4096]
+FIXED_RULES = {"always_1L_ABC": 2, "always_2L_ABC": 8, "always_3L_ABC": 14, "classical": 0}
+
+
+def candidate_name(c: int) -> str:
+    lv, var, tile = B.strassen_selector_candidate(c)
+    if lv == 0:
+        return f"classical/{128 if tile == 0 else 64}"
+    return f"{lv}L {['ABC', 'AB', 'Naive'][var]}/{128 if tile == 0 else 64}"
 
 
 def sweep(out_dir: str) -> List[Dict]:
     """The FP64 shape sweep: square m = n = k in 2048..16384 (step 2048) and rank-k
-    m = n = 16384 with k in 256..4096, every candidate plus three-level ABC, effective
-    GFLOP/s (2mnk/t);
-    writes sweep_fp64.json and sweep_fp64.md into out_dir."""
+    m = n = 16384 with k in 256..4096, every candidate (levels 0-3, variants, tiles),
+    effective GFLOP/s (2mnk/t); writes sweep_fp64.json and sweep_fp64.md into out_dir."""
     import os
     shapes = [(n, n, n) for n in SWEEP_SQUARE] + [(16384, 16384, k) for k in SWEEP_RANKK]
     timer = Timer(16384 * 16384, 16384 * 16384, 16384 * 16384)
-    rows = []
-    for (m, n, k) in shapes:
-        row = measure([(m, n, k)], B.STRASSEN_F64, timer)[0]
-        # three levels (outside the selector's candidate set): ABC only
-        row["three_level_abc"] = timer.time(m, n, k, 3, B.STRASSEN_ABC, B.STRASSEN_F64)
-        rows.append(row)
-    names = ["classical", "1L ABC", "1L AB", "1L Naive", "2L ABC", "2L AB", "2L Naive", "3L ABC"]
+    cs = [0] + [c for c in range(2, NC) if B.strassen_selector_candidate(c)[2] == 0]  # 128-wide tiles
+    rows = measure(shapes, B.STRASSEN_F64, timer, cands=cs)
+    names = [candidate_name(c) for c in cs]
     lines = ["| m | n | k | " + " | ".join(names) + " | best | best / classical |",
              "|" + "---|" * (len(names) + 5)]
     for r in rows:
-        times = list(r["times"]) + [r["three_level_abc"]]
+        times = [r["times"][c] for c in cs]
         eff = [2.0 * r["m"] * r["n"] * r["k"] / t / 1e9 for t in times]
         b = int(np.nanargmin(np.array(times, dtype=np.float64)))
         lines.append(f"| {r['m']} | {r['n']} | {r['k']} | " + " | ".join(f"{v:.0f}" for v in eff) +
@@ -285,31 +327,48 @@ def sweep(out_dir: str) -> List[Dict]:
     return rows
 
 
+def evaluate(params, rows) -> Dict:
+    """Regret of the network, the selection without it (analytic model / classical
+    slices), the fixed rules and exhaustive timing on timed rows."""
+    out = {"mlp": regret(rows, choose_mlp(params, rows)) if params is not None else None,
+           "without_network": regret(rows, choose_model(rows))}
+    for name, c in FIXED_RULES.items():
+        out[name] = regret(rows, choose_fixed(rows, c))
+    out["exhaustive"] = regret(rows, [best_of(r) for r in rows])
+    counts = {}
+    for r in rows:
+        nm = candidate_name(best_of(r))
+        counts[nm] = counts.get(nm, 0) + 1
+    out["best_counts"] = counts
+    return out
+
+
 def main(argv=None) -> int:
-    """Exhaustive timing of seeded random shapes, selector training and held-out
-    evaluation; writes rows, parameters and a regret summary as JSON into --out.
-    With --sweep, runs the FP64 shape sweep instead."""
+    """Exhaustive timing of seeded random shapes (m, n, k log-uniform in [lo, hi]),
+    selector training with the library's kernels and held-out evaluation; writes the
+    timed rows, the parameters and a regret summary as JSON into --out.  Timed rows can
+    be reused (--train-rows, --heldout-rows).  With --sweep, runs the FP64 shape sweep
+    instead."""
     import argparse
     import os
     import sys
     import time
     ap = argparse.ArgumentParser(prog="python -m paper_1605_01078_gb300.tune")
-    ap.add_argument("--train", type=int, default=700, help="FP64 training shapes (seed 1)")
-    ap.add_argument("--heldout", type=int, default=1000, help="FP64 held-out shapes (seed 2)")
-    ap.add_argument("--oz-train", type=int, default=300, help="split-precision training shapes (seed 3)")
-    ap.add_argument("--oz-heldout", type=int, default=200, help="split-precision held-out shapes (seed 4)")
+    ap.add_argument("--train", type=int, default=250, help="FP64 training shapes (seed 1), 20 timings each")
+    ap.add_argument("--heldout", type=int, default=1000, help="FP64 held-out shapes")
+    ap.add_argument("--oz-train", type=int, default=100, help="split-precision training shapes (seed 3)")
+    ap.add_argument("--oz-heldout", type=int, default=200, help="split-precision held-out shapes")
     ap.add_argument("--lo", type=int, default=256)
     ap.add_argument("--hi", type=int, default=16384)
     ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", required=True)
     ap.add_argument("--sweep", action="store_true", help="run the FP64 shape sweep only")
-    ap.add_argument("--train-rows", default=None,
-                    help="train on timed rows saved by an earlier run (JSON) instead of timing training shapes")
+    ap.add_argument("--measure-only", action="store_true", help="time the shapes and save the rows; no training")
+    ap.add_argument("--train-rows", default=None, help="timed training rows saved by an earlier run (JSON)")
+    ap.add_argument("--heldout-rows", default=None, help="timed held-out rows saved by an earlier run (JSON)")
     ap.add_argument("--heldout-seed", type=int, default=2)
     ap.add_argument("--oz-heldout-seed", type=int, default=4)
-    ap.add_argument("--evaluate", default=None,
-                    help="a selector JSON (as shipped in data/): measure only the held-out shapes and report "
-                         "the regret of that network, the analytic model and the fixed rules")
     a = ap.parse_args(argv)
     if a.sweep:
         sweep(a.out)
@@ -319,58 +378,40 @@ def main(argv=None) -> int:
         sys.path.insert(0, root)
     import workloads as W
     os.makedirs(a.out, exist_ok=True)
-    timer = Timer(a.hi * a.hi, a.hi * a.hi, a.hi * a.hi)
+    f64, oz = B.STRASSEN_F64, B.STRASSEN_F64_OZ_BF16
+    timer = None
     t0 = time.time()
-    f64 = B.STRASSEN_F64
-    oz = B.STRASSEN_F64_OZ_BF16
-    if a.evaluate:
-        with open(a.evaluate) as fh:
-            params = np.array(json.load(fh)["params"], dtype=np.float32)
-        held_rows = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, timer)
-        held_oz = measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, timer)
-        summary = {"shapes_heldout_f64": len(held_rows), "shapes_heldout_oz": len(held_oz),
-                   "seconds_measuring": time.time() - t0}
-        for name, rows in (("f64", held_rows), ("oz_bf16", held_oz)):
-            summary[name] = {
-                "mlp": regret(rows, choose_mlp(params, rows)),
-                "analytic_model": regret(rows, choose_model(rows)),
-                "always_1L_ABC": regret(rows, choose_fixed(rows, 1)),
-                "always_2L_ABC": regret(rows, choose_fixed(rows, 4)),
-                "classical": regret(rows, choose_fixed(rows, 0)),
-                "exhaustive": regret(rows, [best_of(r) for r in rows]),
-                "best_counts": {str(c): int(sum(best_of(r) == c for r in rows)) for c in range(7)},
-            }
-        save_rows(os.path.join(a.out, "selector_heldout_rows.json"), held_rows + held_oz)
-        with open(os.path.join(a.out, "selector_evaluation.json"), "w") as fh:
-            json.dump(summary, fh, indent=1)
-        print(json.dumps({k: summary[k] for k in ("f64", "oz_bf16")}, indent=1))
-        return 0
+
+    def get_timer():
+        nonlocal timer
+        if timer is None:
+            timer = Timer(a.hi * a.hi, a.hi * a.hi, a.hi * a.hi)
+        return timer
+
     if a.train_rows:
         train_rows = load_rows(a.train_rows)
     else:
-        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, timer)
-        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, timer)
+        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, get_timer())
+        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, get_timer())
+        save_rows(os.path.join(a.out, "selector_train_rows.json"), train_rows)
     t_train = time.time() - t0
-    held_rows = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, timer)
-    held_oz = measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, timer)
+    if a.heldout_rows:
+        held = load_rows(a.heldout_rows)
+    else:
+        held = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, get_timer())
+        held += measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, get_timer())
+        save_rows(os.path.join(a.out, "selector_heldout_rows.json"), held)
     t_held = time.time() - t0 - t_train
-    params, hist = train(train_rows, steps=a.steps, lr=3e-3, seed=0)
-    summary = {"timings_train": int(sum(np.isfinite(r["times"]).sum() for r in train_rows)),
-               "shapes_train": len(train_rows), "shapes_heldout_f64": len(held_rows),
-               "shapes_heldout_oz": len(held_oz), "seconds_measuring": [t_train, t_held],
-               "loss_history": hist}
-    for name, rows in (("f64", held_rows), ("oz_bf16", held_oz)):
-        summary[name] = {
-            "mlp": regret(rows, choose_mlp(params, rows)),
-            "analytic_model": regret(rows, choose_model(rows)),
-            "always_1L_ABC": regret(rows, choose_fixed(rows, 1)),
-            "always_2L_ABC": regret(rows, choose_fixed(rows, 4)),
-            "classical": regret(rows, choose_fixed(rows, 0)),
-            "exhaustive": regret(rows, [best_of(r) for r in rows]),
-            "best_counts": {str(c): int(sum(best_of(r) == c for r in rows)) for c in range(7)},
-        }
-    save_rows(os.path.join(a.out, "selector_train_rows.json"), train_rows)
-    save_rows(os.path.join(a.out, "selector_heldout_rows.json"), held_rows + held_oz)
+    if a.measure_only:
+        return 0
+    params, hist = train(train_rows, steps=a.steps, lr=a.lr, seed=0)
+    summary = {"timings_train": int(sum(np.isfinite(np.array(r["times"], dtype=float)).sum() for r in train_rows)),
+               "shapes_train": len(train_rows), "seconds_measuring": [t_train, t_held], "loss_history": hist,
+               "steps": a.steps, "lr": a.lr}
+    for name, d in (("f64", f64), ("oz_bf16", oz)):
+        rows = [r for r in held if r["dtype"] == d]
+        summary[name] = evaluate(params, rows)
+        summary[name]["shapes"] = len(rows)
     with open(os.path.join(a.out, "selector_params.json"), "w") as fh:
         json.dump([float(v) for v in params], fh)
     with open(os.path.join(a.out, "selector_summary.json"), "w") as fh:

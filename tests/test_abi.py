@@ -142,6 +142,29 @@ def test_dgemm_ex_flags_checked_on_the_host():
     assert f(0, 0, 0, 4, 4, 1.0, 0, 4, 0, 4, 1.0, 0, 4, 1, 0, 0, 1, 0) == 0
 
 
+def test_batched_rejects_unfused_variants_on_the_host():
+    """A batched problem asking for AB or Naive with one or more levels is refused
+    (the persistent launch runs the fused form only); no device work is attempted."""
+    for variant, levels in ((sg.STRASSEN_AB, 1), (sg.STRASSEN_NAIVE, 2), (sg.STRASSEN_AB, -1)):
+        arr = (sg.strassen_problem * 1)()
+        arr[0] = sg.strassen_problem(8, 8, 8, P, 2 * P, 3 * P, 8, 8, 8, levels, variant)
+        assert sg.strassen_gemm_batched(1, arr, 0, 0) == -5
+
+
+def test_dsyrk_argument_checks_on_the_host():
+    f = sg.strassen_dsyrk
+    assert f(2, 0, 8, 4, 1.0, P, 4, 1.0, 2 * P, 8, 1, 0, 0) == -9        # uplo
+    assert f(0, 2, 8, 4, 1.0, P, 4, 1.0, 2 * P, 8, 1, 0, 0) == -9        # trans
+    assert f(0, 0, 8, 4, 1.0, P, 4, 1.0, 2 * P, 8, 1, 4, 0) == -9        # flags
+    assert f(0, 0, -1, 4, 1.0, P, 4, 1.0, 2 * P, 8, 1, 0, 0) == -1
+    assert f(0, 0, 8, 4, 1.0, P, 3, 1.0, 2 * P, 8, 1, 0, 0) == -2        # lda < k
+    assert f(0, 1, 8, 4, 1.0, P, 4, 1.0, 2 * P, 8, 1, 0, 0) == -2        # A stored 4 x 8: lda >= 8
+    assert f(0, 0, 8, 4, 1.0, P, 4, 1.0, 2 * P, 7, 1, 0, 0) == -2        # ldc < n
+    assert f(0, 0, 8, 4, 1.0, P, 4, 1.0, P + 8, 8, 1, 0, 0) == -9        # C overlaps A
+    assert f(0, 0, 8, 4, 1.0, P, 4, 1.0, 2 * P, 8, 4, 0, 0) == -4
+    assert f(0, 0, 0, 4, 1.0, 0, 4, 1.0, 0, 8, 1, 0, 0) == 0             # empty
+
+
 def test_plain_c_client_compiles_and_runs(tmp_path):
     """The header is plain C (extern "C", C types only): a C99 program includes it, links
     the library and calls its host-side entry points."""

@@ -47,12 +47,14 @@ def test_forward_of_a_hand_built_network():
     for c in range(mlp.N_OUT):
         theta[offs["W3"] + c * mlp.N_H] = float(c)
         theta[offs["b3"] + c] = 0.5
-    X = np.array([[1.5, 0, 0, 1, 0, 0], [-1.0, 0, 0, 0, 1, 0]])
+    X = np.zeros((2, mlp.N_IN))
+    X[0, :6] = [1.5, 0, 0, 1, 0, 0]
+    X[1, :6] = [-1.0, 0, 0, 0, 1, 0]
     y, _ = mlp.forward(theta, X)
     # h1[0] = relu(x0) ; h2[0] = relu(2 h1[0]) ; y_c = c * h2[0] + 0.5
     assert np.allclose(y[0], np.arange(mlp.N_OUT) * 3.0 + 0.5)
     assert np.allclose(y[1], np.full(mlp.N_OUT, 0.5))
-    assert p["W1"].shape == (64, 6)
+    assert p["W1"].shape == (64, 26) and p["W3"].shape == (20, 64)
 
 
 def test_masked_loss_ignores_unmeasured_candidates():
@@ -75,4 +77,7 @@ def test_adam_first_step_is_lr_times_sign():
 
 def test_features():
     x = mlp.features([2048], [256], [16384], [2])
-    assert np.allclose(x, [[0.0, -1.0, 1.0, 0, 0, 1]])
+    assert np.allclose(x[0, :6], [0.0, -1.0, 1.0, 0, 0, 1]) and np.allclose(x[0, 6:], 1.0)
+    b = np.arange(20, dtype=np.float64) - 10.0
+    x = mlp.features([4096], [4096], [4096], [0], base=[b])
+    assert np.allclose(x[0, 6:], (b + 7.0) / 7.0) and x.shape == (1, 26)
