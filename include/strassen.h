@@ -253,14 +253,13 @@ typedef struct {
  *   dtype   STRASSEN_F64.
  *   stream  the CUDA stream.
  *
- * Problems with the same tile and level share one persistent launch (the kernel
- * instance sized for that level's term count), so the call makes one launch per
- * (tile, level) group in use, at most eight.  Within a launch the work units (problem,
- * product, tile, k-steps) are claimed in chunks from a counter, and partial products
- * are added into C with device atomics.  With several groups the launches go largest
- * first, alternately on `stream` and on a library stream forked from it with an event
- * (so one launch's tail overlaps the next launch's start); `stream` waits for both
- * before the call's work counts as done.  The work list travels in kernel parameters
+ * Problems with the same tile share one persistent launch, so the call makes one launch
+ * per tile in use (at most two).  Within a launch the thread blocks claim whole work
+ * units (problem, product, output tile, all of its k) from a counter, problems with the
+ * longest units first, and add their partial products into C with device atomics.
+ * With two launches the larger goes first on `stream` and the other on a library stream
+ * forked from it with an event (so one launch's tail overlaps the other's start);
+ * `stream` waits for both before the call's work counts as done.  The work list travels in kernel parameters
  * to a small kernel that writes it into a stream-ordered temporary (cudaMallocAsync),
  * so the whole call can be captured in a CUDA graph and replayed; make one call on the
  * device outside a capture first (it creates the library stream).  Returns STRASSEN_OK
@@ -276,8 +275,9 @@ STRASSEN_API int strassen_gemm_batched(int count, const strassen_problem* probs,
  * the paper builds its performance model for.  In order of precedence it returns
  *   1. the exhaustive-measurement record for exactly this shape and dtype, if one was
  *      stored with strassen_tune_record();
- *   2. the argmin of the learned selector's predictions over its 20 candidates (every
- *      level 0-3, variant and tile; see strassen_selector_candidate), if a network was
+ *   2. the argmin of the learned selector's predictions over its 16 candidates (levels
+ *      0-2 of every variant and three-level ABC, each with both tiles; see
+ *      strassen_selector_candidate), if a network was
  *      loaded with strassen_selector_load() and is enabled for the dtype.  The first
  *      choice for a shape runs one small kernel on a library stream and waits for it;
  *      the choice is cached, so later calls for the shape do no GPU work;
@@ -317,21 +317,21 @@ STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int 
 
 /*
  * The learned selector (not in the paper; it stands in for the analytic model of
- * Section 4.2).  A multilayer perceptron 26 -> 64 -> 64 -> 20 (FP32, ReLU) maps a
+ * Section 4.2).  A multilayer perceptron 22 -> 64 -> 64 -> 16 (FP32, ReLU) maps a
  * shape's features to a correction of the analytic model's log2 seconds for each of
- * STRASSEN_SELECTOR_CANDIDATES = 20 candidates; the selection is the argmin over the
+ * STRASSEN_SELECTOR_CANDIDATES = 16 candidates; the selection is the argmin over the
  * dtype's valid candidates of (model log2 seconds + correction).  Features, from
  * strassen_selector_features: (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype
  * one-hot, then for every candidate (model log2 seconds + 7)/7.  Candidates
  * (strassen_selector_candidate): 0, 1 classical with tile 0, 1; 2 + 6 (L - 1) + 2 v + t
- * for L levels (1-3), variant v (ABC, AB, Naive) and tile t.  The split-precision dtype
- * uses the tile-0 ABC candidates (0, 2, 8, 14).  Its parameters are one float vector of
- * strassen_mlp_param_count() entries: [W1 (64x26 row-major), b1 (64), W2 (64x64),
- * b2 (64), W3 (20x64), b3 (20)].
+ * for L levels (1, 2), variant v (ABC, AB, Naive) and tile t; 14 + t three-level ABC.
+ * The split-precision dtype uses the tile-0 ABC candidates (0, 2, 8, 14: levels 0-3).
+ * Its parameters are one float vector of strassen_mlp_param_count() entries:
+ * [W1 (64x22 row-major), b1 (64), W2 (64x64), b2 (64), W3 (16x64), b3 (16)].
  *
- * strassen_mlp_forward   Y[batch][20] = network(X[batch][26]); all DEVICE pointers.
+ * strassen_mlp_forward   Y[batch][16] = network(X[batch][22]); all DEVICE pointers.
  * strassen_mlp_loss_grad grad = d/dparams of sum mask (Y - T)^2 / mask_sum over the
- *                        batch (X [batch][26], T and mask [batch][20], DEVICE); grad is
+ *                        batch (X [batch][22], T and mask [batch][16], DEVICE); grad is
  *                        overwritten.  mask_sum > 0 is the sum of mask.  For training,
  *                        T = log2 measured seconds - the model's log2 seconds.
  * strassen_mlp_adam      one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1)
@@ -343,15 +343,15 @@ STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int 
  *                        (default: all enabled); with it disabled, strassen_select()
  *                        falls through to the analytic model for that dtype.  The tuning
  *                        driver enables it only where it beat the model on held-out shapes.
- * strassen_selector_candidate  (levels, variant, tile_id) of candidate c (0..19).
- * strassen_selector_features   x[26] (network inputs), base[20] (the model's log2
+ * strassen_selector_candidate  (levels, variant, tile_id) of candidate c (0..15).
+ * strassen_selector_features   x[22] (network inputs), base[16] (the model's log2
  *                        seconds) and the bit mask of the candidates valid for `dtype`,
  *                        on the host (no GPU work; the model reads the device's SM
  *                        count and clock).
  * All return STRASSEN_OK or a negative status; the kernels run on `stream`.
  */
-#define STRASSEN_SELECTOR_CANDIDATES 20
-#define STRASSEN_SELECTOR_INPUTS 26
+#define STRASSEN_SELECTOR_CANDIDATES 16
+#define STRASSEN_SELECTOR_INPUTS 22
 STRASSEN_API int strassen_mlp_param_count(void);
 STRASSEN_API int strassen_mlp_forward(const float* params, const float* X, int batch, float* Y,
                                       strassen_stream_t stream);

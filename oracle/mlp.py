@@ -3,11 +3,11 @@
 Not a method of the paper: a small network standing in for the paper's analytical
 performance model (Section 4.2) in choosing a member of the family.  Definition:
 
-    x  (26)  features: (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype one-hot (3),
-             then (b_c + 7)/7 for the 20 candidates, b_c the analytic model's log2 seconds
-    h1 = relu(W1 x + b1)      W1: 64 x 26
+    x  (22)  features: (log2 m - 11)/3, (log2 n - 11)/3, (log2 k - 11)/3, dtype one-hot (3),
+             then (b_c + 7)/7 for the 16 candidates, b_c the analytic model's log2 seconds
+    h1 = relu(W1 x + b1)      W1: 64 x 22
     h2 = relu(W2 h1 + b2)     W2: 64 x 64
-    y  = W3 h2 + b3           W3: 20 x 64  (the correction to b_c: predicted log2 seconds
+    y  = W3 h2 + b3           W3: 16 x 64  (the correction to b_c: predicted log2 seconds
                                             of candidate c are b_c + y_c)
 
     loss = sum_{i,c} mask_ic (y_ic - t_ic)^2 / sum_{i,c} mask_ic
@@ -19,7 +19,7 @@ from __future__ import annotations
 
 import numpy as np
 
-N_SHAPE, N_OUT, N_H = 6, 20, 64
+N_SHAPE, N_OUT, N_H = 6, 16, 64
 N_IN = N_SHAPE + N_OUT
 SHAPES = [("W1", (N_H, N_IN)), ("b1", (N_H,)), ("W2", (N_H, N_H)), ("b2", (N_H,)),
           ("W3", (N_OUT, N_H)), ("b3", (N_OUT,))]
@@ -37,7 +37,7 @@ def unpack(theta: np.ndarray) -> dict:
 
 def features(m, n, k, dtype, base=None) -> np.ndarray:
     """Feature rows for arrays of sizes, dtype codes (0 FP64, 1 INT8 split, 2 BF16 split)
-    and the model's log2 seconds per candidate `base` [rows, 20] (zeros when None)."""
+    and the model's log2 seconds per candidate `base` [rows, 16] (zeros when None)."""
     m, n, k, dtype = (np.atleast_1d(np.asarray(v)) for v in (m, n, k, dtype))
     x = np.zeros((m.size, N_IN))
     x[:, 0] = (np.log2(m) - 11.0) / 3.0

@@ -216,7 +216,7 @@ def strassen_selector_clear() -> int:
     return lib().strassen_selector_clear()
 
 
-SELECTOR_CANDIDATES, SELECTOR_INPUTS = 20, 26  # STRASSEN_SELECTOR_CANDIDATES / _INPUTS
+SELECTOR_CANDIDATES, SELECTOR_INPUTS = 16, 22  # STRASSEN_SELECTOR_CANDIDATES / _INPUTS
 
 
 def strassen_selector_candidate(c):
@@ -228,7 +228,7 @@ def strassen_selector_candidate(c):
 
 
 def strassen_selector_features(m, n, k, dtype):
-    """(x[26], base[20], valid mask) of a shape: the network's inputs, the analytic
+    """(x[22], base[16], valid mask) of a shape: the network's inputs, the analytic
     model's log2 seconds per candidate and the candidates valid for the dtype."""
     x = (ctypes.c_float * SELECTOR_INPUTS)()
     base = (ctypes.c_float * SELECTOR_CANDIDATES)()

@@ -474,13 +474,11 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
       cudaGetLastError();
       return STRASSEN_ERR_CUDA;
     }
-    // One persistent launch per (tile, levels) group -- the kernel instance fits the
-    // group's term count and tile -- issued largest first, alternately on the caller's
-    // stream and a library side stream forked from it, so that each launch's tail
-    // overlaps the next launch's start; the caller's stream waits for both at the end.
-    std::stable_sort(launches.begin(), launches.end(), [](const Fp64Launch& a, const Fp64Launch& b) {
-      return a.tile != b.tile ? a.tile < b.tile : a.levels < b.levels;
-    });
+    // One persistent launch per block tile in use, the larger first, the second on a
+    // library stream forked from the caller's, so that the first launch's tail overlaps
+    // the second's start; the caller's stream waits for both at the end.
+    std::stable_sort(launches.begin(), launches.end(),
+                     [](const Fp64Launch& a, const Fp64Launch& b) { return a.tile < b.tile; });
     struct Group {
       size_t begin, end;
       double work;
@@ -490,7 +488,7 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
     for (size_t i = 0; i < launches.size();) {
       size_t j = i;
       double w = 0.0;
-      while (j < launches.size() && launches[j].tile == launches[i].tile && launches[j].levels == launches[i].levels) {
+      while (j < launches.size() && launches[j].tile == launches[i].tile) {
         w += fp64_launch_estimate(launches[j], launches[j].tile, 1);
         ++j;
       }

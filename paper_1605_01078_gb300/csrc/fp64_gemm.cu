@@ -33,8 +33,8 @@
 // memory; every wait is bounded (about one second of clock cycles), after which the
 // kernel records STRASSEN_ERR_TIMEOUT in a device status word and returns instead of
 // hanging.  A single launch gives each block one stream-K range (or its tiles under
-// the owner schedule); a batched launch lets blocks claim chunks of the stream-K space
-// from a global counter.
+// the owner schedule); a batched launch lets blocks claim whole work units, longest
+// first, from a global counter.
 //
 // GB300 design notes.  FP64 runs at about 2 FMA lanes per clock per SM (measured
 // 1.20 TFLOP/s for the whole GPU; DMMA is slower at 1.06), so this kernel is bound by
@@ -105,6 +105,7 @@ struct alignas(128) ProbDesc {
   int64_t a_rows, a_cols, b_rows, b_cols, c_rows, c_cols;
   int64_t hm, hn, hk;
   int64_t iter_begin;  // first iteration of this problem in the stream-K space
+  int64_t unit_begin;  // batched: index of this problem's first work unit
   int32_t plan_row;    // table row of the first product of this problem
   int32_t nprod;
   int32_t m_target;
@@ -120,12 +121,11 @@ struct alignas(128) ProbDesc {
 struct KArgs {
   ProbDesc single;         // the problem when not batched
   const ProbDesc* descs;   // device array when batched
-  unsigned long long* chunk_counter;  // batched: next chunk to claim (cleared before the launch)
+  unsigned long long* chunk_counter;  // batched: next unit to claim (cleared before the launch)
   int nprob;
   int sched;
   int64_t total;           // stream-K: iterations of all problems; owner: tile positions
-  int64_t chunk;           // batched: iterations per claimed chunk
-  int64_t nchunks;
+  int64_t nchunks;         // batched: work units to claim (one claim = one whole unit)
   int64_t dp_rounds;       // single stream-K launch: rounds of whole units before the split tail
 };
 
@@ -215,18 +215,27 @@ __device__ __forceinline__ const ProbDesc& desc_of(const KArgs& a, int p) {
   else return a.single;
 }
 
-// Cursor on range `id` of the work: batched launches claim chunks of `chunk`
-// iterations of the stream-K space; single launches have one range per block (a
-// stream-K share, or the block's tile positions under the owner schedule).
+// Cursor on range `id` of the work: a batched launch claims one whole unit per id;
+// single launches have one range per block (a stream-K share, or the block's tile
+// positions under the owner schedule).
 template <bool BATCHED>
 __device__ Cursor range_cursor(const KArgs& a, int64_t id) {
   Cursor c;
   c.p = 0; c.r = 0; c.t = 0; c.ks = 0; c.left = 0;
   if (BATCHED || a.sched == kSchedStreamK) {
     int64_t beg, end;
+    int p = 0;
     if constexpr (BATCHED) {
-      beg = id * a.chunk;
-      end = beg + a.chunk < a.total ? beg + a.chunk : a.total;
+      // Claim `id` is one whole unit: problem p is the last whose first unit is <= id.
+      int lo = 0, hi = a.nprob - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (a.descs[mid].unit_begin <= id) lo = mid; else hi = mid - 1;
+      }
+      p = lo;
+      const ProbDesc& dp = a.descs[p];
+      beg = dp.iter_begin + (id - dp.unit_begin) * dp.ksteps;
+      end = beg + dp.ksteps;
     } else {
       // Claims 0 .. dp_rounds - 1: whole units, round-robin over the blocks, so the
       // blocks of one round work on neighbouring tiles of the same product at the same
@@ -244,15 +253,6 @@ __device__ Cursor range_cursor(const KArgs& a, int64_t id) {
     }
     c.left = end - beg;
     if (c.left > 0) {
-      int p = 0;
-      if constexpr (BATCHED) {  // last problem whose first iteration is <= beg
-        int lo = 0, hi = a.nprob - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (a.descs[mid].iter_begin <= beg) lo = mid; else hi = mid - 1;
-        }
-        p = lo;
-      }
       const ProbDesc& d = desc_of<BATCHED>(a, p);
       const int64_t local = beg - d.iter_begin;
       const int64_t u = local / d.ksteps;
@@ -669,7 +669,16 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       const int nc = d.m_target ? 1 : (int)c_plans.nc[row];
       const int tm = m.t / d.tiles_n, tn = m.t - (m.t / d.tiles_n) * d.tiles_n;
       const int warp = tid >> 5, lane = tid & 31;
-      const double alpha = d.alpha;  // exact no-op for alpha = 1
+      // The BLAS form's alpha scales the partial sum here; alpha = 1 (the plain
+      // operation) skips the multiplies, which would otherwise take FP64-pipe slots
+      // from the multiply-adds at every flush.
+      if (d.alpha != 1.0) {
+        const double alpha = d.alpha;
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] *= alpha;
+      }
       double* stage = epi_stage + warp * (2 * BN);
       const int half = ty - 2 * warp;  // which of the warp's two thread rows
 #pragma unroll
@@ -678,8 +687,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
         double2* dst1 = reinterpret_cast<double2*>(stage + half * BN + BN / 2 + tx * (TN / 2));
 #pragma unroll
         for (int v = 0; v < TN / 4; ++v) {
-          dst0[v] = make_double2(alpha * acc[i][2 * v], alpha * acc[i][2 * v + 1]);
-          dst1[v] = make_double2(alpha * acc[i][TN / 2 + 2 * v], alpha * acc[i][TN / 2 + 2 * v + 1]);
+          dst0[v] = make_double2(acc[i][2 * v], acc[i][2 * v + 1]);
+          dst1[v] = make_double2(acc[i][TN / 2 + 2 * v], acc[i][TN / 2 + 2 * v + 1]);
         }
         __syncwarp();
         // Local tile rows of this row group for the warp's two thread rows.
@@ -943,7 +952,6 @@ namespace {
 // descriptors -- TMA tensor maps encoded on the host included -- into the device
 // array the persistent kernel reads.
 constexpr int kDescPerExpand = (32000 - 64) / (int)sizeof(ProbDesc);
-constexpr int kChunksPerBlock = 64;
 struct ExpandArgs {
   ProbDesc* out;
   unsigned long long* counter;  // cleared when not null
@@ -995,7 +1003,6 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   }
   std::vector<ProbDesc> descs;
   descs.reserve(count);
-  int64_t total = 0;
   int cls = 0;
   for (int i = 0; i < count; ++i) {
     ProbDesc d;
@@ -1005,10 +1012,21 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
     L.tile = tile;
     fill_desc(L, &d);
     if (d.nprod <= 0 || d.ksteps <= 0 || d.tiles_m <= 0 || d.tiles_n <= 0) continue;
-    d.iter_begin = total;
-    total += (int64_t)d.nprod * d.tiles_m * d.tiles_n * d.ksteps;
     cls = std::max(cls, term_class_of(L.levels, L.prod_begin, d.nprod));
     descs.push_back(d);
+  }
+  // Longest units first (a claim is one whole unit, so the last claims, which set the
+  // tail, are the shortest); within a problem the units go product by product, tile by
+  // tile, so the blocks that run at the same time work on neighbouring tiles of one
+  // product at about the same k and share operand tiles in the L2.
+  std::stable_sort(descs.begin(), descs.end(), [](const ProbDesc& x, const ProbDesc& y) { return x.ksteps > y.ksteps; });
+  int64_t total = 0, units = 0;
+  for (ProbDesc& d : descs) {
+    d.iter_begin = total;
+    d.unit_begin = units;
+    const int64_t nu = (int64_t)d.nprod * d.tiles_m * d.tiles_n;
+    units += nu;
+    total += nu * d.ksteps;
   }
   if (descs.empty()) return cudaSuccess;
   ProbDesc* dev = (ProbDesc*)scratch;
@@ -1032,10 +1050,7 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   args.nprob = (int)descs.size();
   args.sched = kSchedStreamK;
   args.total = total;
-  // Chunks of about 1/64 of a block's even share: blocks that meet cheaper iterations
-  // (fewer C targets per unit, TMA instead of cp.async staging) claim more of them.
-  args.chunk = std::max<int64_t>(1, (total + (int64_t)sms * kChunksPerBlock - 1) / ((int64_t)sms * kChunksPerBlock));
-  args.nchunks = (total + args.chunk - 1) / args.chunk;
+  args.nchunks = units;  // blocks claim whole units until none are left
   const int64_t grid = std::min<int64_t>(sms, args.nchunks);
   void* kargs[] = {&args};
   return cudaLaunchKernel(pick_kernel(cls, true, tile), dim3((unsigned)grid), dim3(kThreads), kargs,

@@ -149,9 +149,10 @@ int ozaki_device_status();
 double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels);
 
 // Learned selector (mlp.cu).  Candidates: c = 0, 1 classical with tile c; c = 2 + 6 (L - 1)
-// + 2 v + t: L levels (1..3) of variant v (ABC, AB, Naive) with tile t.  The split-precision
-// dtype takes the tile-0 ABC candidates only (levels 0..3).
-constexpr int kSelCandidates = 2 + 6 * kMaxLevels;
+// + 2 v + t: L levels (1, 2) of variant v (ABC, AB, Naive) with tile t; c = 14 + t: three
+// levels of ABC with tile t.  The split-precision dtype takes the tile-0 ABC candidates
+// only (0, 2, 8, 14: levels 0..3).
+constexpr int kSelCandidates = 16;
 constexpr int kSelInputs = 6 + kSelCandidates;
 void selector_candidate(int c, int* levels, int* variant, int* tile);
 bool selector_candidate_valid(int c, int dtype);

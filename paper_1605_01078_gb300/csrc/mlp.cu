@@ -1,6 +1,6 @@
-// Learned variant selector: a small MLP (26 -> 64 -> 64 -> 20, FP32, ReLU) that
-// predicts, for each of 20 candidates -- classical, and 1, 2 or 3 levels of ABC, AB and
-// Naive, each with the 128x128 or the 64x64 block tile -- the log2 run time of a shape
+// Learned variant selector: a small MLP (22 -> 64 -> 64 -> 16, FP32, ReLU) that
+// predicts, for each of 16 candidates -- classical, 1 or 2 levels of ABC, AB and Naive,
+// and 3 levels of ABC, each with the 128x128 or the 64x64 block tile -- the log2 run time of a shape
 // as a correction to the analytic performance model's prediction.  Its inputs are
 // log2 m, log2 n, log2 k, the dtype and the model's log2 seconds for every candidate
 // (which carry the padding of each tile, invisible in the sizes alone).  It stands in
@@ -11,8 +11,8 @@
 // per-block gradient sums in shared memory, one atomic add per parameter per block),
 // Adam, and the single-shape selection used by strassen_select().
 //
-// Parameter vector (float): [W1 (64x26, row-major), b1 (64), W2 (64x64), b2 (64),
-// W3 (20x64), b3 (20)].  Loss: masked mean squared error over measured candidates of
+// Parameter vector (float): [W1 (64x22, row-major), b1 (64), W2 (64x64), b2 (64),
+// W3 (16x64), b3 (16)].  Loss: masked mean squared error over measured candidates of
 // (network output - (log2 measured seconds - model log2 seconds)).
 #include <cuda_runtime.h>
 
@@ -186,10 +186,10 @@ int grid_for_batch(int batch) { return batch < 1 ? 1 : (batch < 1024 ? batch : 1
 }  // namespace
 
 void selector_candidate(int c, int* levels, int* variant, int* tile) {
-  if (c < 2) {
-    *levels = 0;
+  if (c < 2 || c >= 14) {
+    *levels = c < 2 ? 0 : 3;
     *variant = STRASSEN_ABC;
-    *tile = c < 0 ? 0 : c;
+    *tile = c < 0 ? 0 : c % 2;
     return;
   }
   const int r = c - 2;

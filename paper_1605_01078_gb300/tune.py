@@ -40,7 +40,7 @@ DTYPE_NAME = {B.STRASSEN_F64: "f64", B.STRASSEN_F64_OZ_BF16: "oz_bf16"}
 
 
 def features(rows) -> Tuple[np.ndarray, np.ndarray]:
-    """Network inputs X [rows, 26] and the analytic model's log2 seconds [rows, 20], as
+    """Network inputs X [rows, 22] and the analytic model's log2 seconds [rows, 16], as
     the library computes them (strassen_selector_features)."""
     X = np.zeros((len(rows), B.SELECTOR_INPUTS), dtype=np.float32)
     base = np.zeros((len(rows), NC), dtype=np.float32)
@@ -100,10 +100,11 @@ class Timer:
 
 
 def measure(shapes: Sequence[Tuple[int, int, int]], dtype: int, timer: Timer,
-            cands: Optional[Sequence[int]] = None) -> List[Dict]:
+            cands: Optional[Sequence[int]] = None, log_path: Optional[str] = None) -> List[Dict]:
     """Exhaustive timing: one row per shape with the seconds of every valid candidate
     (NaN for the others).  Candidates whose levels would be clamped for the shape are
-    timed as what they run."""
+    timed as what they run.  With log_path, every row is also appended to that file as
+    one JSON line as soon as it is measured."""
     cl = candidates()
     cs = list(valid_candidates(dtype) if cands is None else cands)
     rows = []
@@ -112,7 +113,11 @@ def measure(shapes: Sequence[Tuple[int, int, int]], dtype: int, timer: Timer,
         for c in cs:
             lv, var, tile = cl[c]
             times[c] = timer.time(m, n, k, lv, var, tile, dtype)
-        rows.append({"m": int(m), "n": int(n), "k": int(k), "dtype": int(dtype), "times": times})
+        row = {"m": int(m), "n": int(n), "k": int(k), "dtype": int(dtype), "times": times}
+        rows.append(row)
+        if log_path:
+            with open(log_path, "a") as fh:
+                fh.write(json.dumps(row) + "\n")
     return rows
 
 
@@ -285,7 +290,10 @@ def save_rows(path: str, rows) -> None:
 
 
 def load_rows(path: str):
+    """Timed rows from a JSON list, or from a file of one JSON row per line (.jsonl)."""
     with open(path) as fh:
+        if path.endswith(".jsonl"):
+            return [json.loads(line) for line in fh if line.strip()]
         return json.load(fh)
 
 
@@ -391,15 +399,18 @@ def main(argv=None) -> int:
     if a.train_rows:
         train_rows = load_rows(a.train_rows)
     else:
-        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, get_timer())
-        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, get_timer())
+        log = os.path.join(a.out, "selector_train_rows.jsonl")
+        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, get_timer(), log_path=log)
+        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, get_timer(), log_path=log)
         save_rows(os.path.join(a.out, "selector_train_rows.json"), train_rows)
     t_train = time.time() - t0
     if a.heldout_rows:
         held = load_rows(a.heldout_rows)
     else:
-        held = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, get_timer())
-        held += measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, get_timer())
+        log = os.path.join(a.out, "selector_heldout_rows.jsonl")
+        held = measure(W.loguniform_shapes(a.heldout, a.heldout_seed, a.lo, a.hi), f64, get_timer(), log_path=log)
+        held += measure(W.loguniform_shapes(a.oz_heldout, a.oz_heldout_seed, a.lo, a.hi), oz, get_timer(),
+                        log_path=log)
         save_rows(os.path.join(a.out, "selector_heldout_rows.json"), held)
     t_held = time.time() - t0 - t_train
     if a.measure_only:

@@ -3,7 +3,8 @@ shipped network's gain over the selection without it on the committed held-out t
 
 The selection without the network is the analytic model (FP64) or classical slices
 (split precision).  The network predicts a correction to the model's log2 seconds for
-each of the 20 candidates (levels 0-3, variants ABC/AB/Naive, 128- or 64-wide tiles).
+each of the 16 candidates (levels 0-2 of ABC/AB/Naive and three-level ABC, each with the
+128- or 64-wide tile).
 """
 import json
 import os
@@ -23,7 +24,7 @@ DATA = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 
 
 def test_training_on_live_timings():
-    """Exhaustive timing of 32 small seeded shapes (all 20 candidates), full-batch Adam
+    """Exhaustive timing of 32 small seeded shapes (all 16 candidates), full-batch Adam
     with the library's kernels: the loss falls, and once loaded, strassen_select returns
     the network's argmin."""
     shapes = W.loguniform_shapes(32, seed=11, lo=128, hi=2048)

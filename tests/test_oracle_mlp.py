@@ -54,7 +54,7 @@ def test_forward_of_a_hand_built_network():
     # h1[0] = relu(x0) ; h2[0] = relu(2 h1[0]) ; y_c = c * h2[0] + 0.5
     assert np.allclose(y[0], np.arange(mlp.N_OUT) * 3.0 + 0.5)
     assert np.allclose(y[1], np.full(mlp.N_OUT, 0.5))
-    assert p["W1"].shape == (64, 26) and p["W3"].shape == (20, 64)
+    assert p["W1"].shape == (64, 22) and p["W3"].shape == (16, 64)
 
 
 def test_masked_loss_ignores_unmeasured_candidates():
@@ -78,6 +78,6 @@ def test_adam_first_step_is_lr_times_sign():
 def test_features():
     x = mlp.features([2048], [256], [16384], [2])
     assert np.allclose(x[0, :6], [0.0, -1.0, 1.0, 0, 0, 1]) and np.allclose(x[0, 6:], 1.0)
-    b = np.arange(20, dtype=np.float64) - 10.0
+    b = np.arange(16, dtype=np.float64) - 10.0
     x = mlp.features([4096], [4096], [4096], [0], base=[b])
-    assert np.allclose(x[0, 6:], (b + 7.0) / 7.0) and x.shape == (1, 26)
+    assert np.allclose(x[0, 6:], (b + 7.0) / 7.0) and x.shape == (1, 22)
