@@ -7,7 +7,7 @@ the FP64 shape sweep.  One step = one strassen_gemm call through the C ABI on in
 resident in HBM (6 GB of operands, larger than the 129 MB L2, so no flush is needed
 between steps).
 
-Metric: effective GFLOPS = 2mnk / t * 1e-9 (the paper's effective GFLOPS of Section 5).
+Metric: effective GFLOPS = 2mnk / t * 1e-9 (the paper's effective GFLOPS, Section 4.2).
 Also reported: the library's classical FP64 kernel on the same inputs (the comparator),
 the same call with STRASSEN_FLAG_DETERMINISTIC (owner schedule), the strict max-norm
 error max|C - C_exact| / (max|A| max|B|) and the Frobenius error of one call on sampled
@@ -324,6 +324,22 @@ def bench_batched(sg, W, torch, reps=3):
             "loop_of_classical": {"value": flops / t_loop / 1e9, "ms": t_loop * 1e3, "launches": len(mats)},
             "loop_of_auto_calls": {"value": flops / t_auto / 1e9, "ms": t_auto * 1e3, "calls": len(mats)},
             "speedup_vs_loop": t_loop / t_graph}
+
+
+def bench_syrk(sg, W, torch, n=8192, k=8192, reps=3):
+    """The level-3 BLAS user: C = A A^T + C on the lower triangle (strassen_dsyrk) at
+    n x k, effective GFLOP/s = n (n + 1) k / t (the flops of the triangle), with the
+    selector's Strassen plans on the off-diagonal blocks and with classical products only
+    (levels 0)."""
+    A, C = W.uniform_device(n, k, 41), W.uniform_device(n, n, 42)
+    s = torch.cuda.current_stream()
+    out = {"workload": f"DSYRK lower, n={n}, k={k}, A, C uniform[-1,1], C += A A^T on the triangle"}
+    for name, lv in (("auto", -1), ("two_levels", 2), ("classical", 0)):
+        t = timed_calls(torch, lambda: sg.dsyrk(A, C, levels=lv, stream=s), reps, s)
+        out[name] = {"value": n * (n + 1.0) * k / t / 1e9, "unit": UNIT, "ms": t * 1e3}
+    del A, C
+    torch.cuda.empty_cache()
+    return out
 
 
 def split_tensor_flops(m, n, k, L):
@@ -643,6 +659,9 @@ def main():
     batched = None
     if not args.no_batched and rank == 0:
         batched = bench_batched(sg, W, torch)
+    syrk = None
+    if not args.no_levels and args.dtype == "f64" and rank == 0:
+        syrk = bench_syrk(sg, W, torch)
     split = None
     if not args.no_split and rank == 0:
         split = bench_split_precision(sg, W, torch, with_errors=not args.no_accuracy)
@@ -692,6 +711,7 @@ def main():
         "other_levels": levels_other,
         "small_square": small,
         "batched": batched,
+        "syrk": syrk,
         "split_precision": split,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,

@@ -1,7 +1,8 @@
 """CPU oracle for Strassen-fused GEMM (Huang, Smith, Henry, van de Geijn 2016).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  It shares no code with the
+CPU leg of ``bench.py`` (the CPU baseline and the exact and textbook entries behind its
+error figures) may import this package.  It shares no code with the
 CUDA library in ``paper_1605_01078_gb300`` and never imports it.
 
 Contents

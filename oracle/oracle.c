@@ -2,8 +2,9 @@
  * CPU oracle for the GEMM / Strassen hot path.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library includes, links or calls
- * this file; only the tests, the smoke check and the CPU-baseline leg of the
- * benchmark load it.  It shares no code, header or table with the CUDA path.
+ * this file; only the tests, the smoke check and the CPU leg of the benchmark (its
+ * baseline timing and the reference entries of its error figures) load it.  It shares
+ * no code, header or table with the CUDA path.
  *
  * Everything is plain IEEE double arithmetic, row-major, one thread, written to be
  * checked against the paper by eye rather than to be fast (a second build with OpenMP,

@@ -57,7 +57,7 @@ __global__ void combine_kernel(const __grid_constant__ CombineParams p) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / p.hn, j = e - (e / p.hn) * p.hn;
-    const double m = p.alpha * p.M[e];  // exact for alpha = 1
+    const double m = p.alpha == 1.0 ? p.M[e] : p.alpha * p.M[e];  // no FP64 multiply for alpha = 1
     for (int t = 0; t < p.ntargets; ++t) {
       const uint8_t c = p.targets[t];
       const int64_t gr = (int64_t)term_bi(c) * p.hm + i, gc = (int64_t)term_bj(c) * p.hn + j;

@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(256) oz_recombine_scatter(const __grid_constan
           group_total(a, r, i, j, &th, &tl);
           const double M = round_i128(th, tl,
                                       a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
-          const double aM = a.alpha * M;  // exact for alpha = 1
+          const double aM = a.alpha == 1.0 ? M : a.alpha * M;  // no FP64 multiply for alpha = 1
           c = (a.upd[u] & 1) ? c - aM : c + aM;
         }
         *cp = c;

@@ -375,6 +375,9 @@ def main(argv=None) -> int:
     ap.add_argument("--measure-only", action="store_true", help="time the shapes and save the rows; no training")
     ap.add_argument("--train-rows", default=None, help="timed training rows saved by an earlier run (JSON)")
     ap.add_argument("--heldout-rows", default=None, help="timed held-out rows saved by an earlier run (JSON)")
+    ap.add_argument("--train-skip", type=int, default=0,
+                    help="skip the first N FP64 training shapes (already timed), time the rest of --train")
+    ap.add_argument("--oz-train-skip", type=int, default=0, help="the same for the split-precision training shapes")
     ap.add_argument("--heldout-seed", type=int, default=2)
     ap.add_argument("--oz-heldout-seed", type=int, default=4)
     a = ap.parse_args(argv)
@@ -400,8 +403,10 @@ def main(argv=None) -> int:
         train_rows = load_rows(a.train_rows)
     else:
         log = os.path.join(a.out, "selector_train_rows.jsonl")
-        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi), f64, get_timer(), log_path=log)
-        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi), oz, get_timer(), log_path=log)
+        train_rows = measure(W.loguniform_shapes(a.train, 1, a.lo, a.hi)[a.train_skip:], f64, get_timer(),
+                             log_path=log)
+        train_rows += measure(W.loguniform_shapes(a.oz_train, 3, a.lo, a.hi)[a.oz_train_skip:], oz, get_timer(),
+                              log_path=log)
         save_rows(os.path.join(a.out, "selector_train_rows.json"), train_rows)
     t_train = time.time() - t0
     if a.heldout_rows:
