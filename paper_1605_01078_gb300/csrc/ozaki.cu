@@ -17,7 +17,8 @@
 //      chunk holds at most 256 of them (|sum| <= 2^22), so the tensor-core accumulator
 //      stays exact; the epilogue warps convert each chunk to int32 and sum the chunks of
 //      a weight (at most 16384 k per segment keeps the sum below 2^31);
-//   3. recombine + scatter (oz_recombine_scatter): T = sum_w G_w 2^(8(8-w)) exactly in
+//   3. recombine + scatter (oz_recombine_local up to two levels, oz_recombine_scatter
+//      at three): T = sum_w G_w 2^(8(8-w)) exactly in
 //      128-bit integers (Horner over w, segments added), M = RN(T) 2^(e_i + f_j - 64)
 //      with a single round-to-nearest-even conversion (integer operations), and
 //      C_q = C_q + gamma_q M_r for every product in table order (the ABC scatter, one
@@ -147,6 +148,8 @@ struct SplitArgs {
   int trans;                // the source is stored transposed (element (r, c) at src[c * ld + r])
   __nv_bfloat16* slices;    // [P][S][h_outp][h_kp]
   int* exps;                // [P][h_outp]
+  unsigned long long* vsum; // B side: [P][h_k][h_out] bits of the operand sums with more than one
+                            // term, written by oz_colmax and read by oz_split_cols (null: none)
 };
 
 // One block per output row i of X^ (rows of A's operand sum), product blockIdx.y.
@@ -211,9 +214,15 @@ __global__ void __launch_bounds__(256) oz_colmax(const __grid_constant__ SplitAr
   for (int t = 0; t < kMaxTerms; ++t) terms[t] = c_oz_plans.tb[row][t];
   const int tid = threadIdx.x, c = tid & 63, ph = tid >> 6;
   unsigned long long mx = 0;
+  // Sums of several terms are kept for oz_split_cols, which then reads one value
+  // instead of forming the sum again.
+  unsigned long long* keep = (nt > 1 && a.vsum) ? a.vsum + (int64_t)p * a.h_k * a.h_out : nullptr;
   if (j0 + c < a.h_out)
-    for (int64_t k = kb + ph; k < ke; k += 4)
-      mx = max(mx, mag_bits(operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j0 + c, a.trans)));
+    for (int64_t k = kb + ph; k < ke; k += 4) {
+      const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j0 + c, a.trans);
+      if (keep) keep[k * a.h_out + j0 + c] = x;
+      mx = max(mx, mag_bits(x));
+    }
   red[ph][c] = mx;
   __syncthreads();
   if (tid < 64) {
@@ -259,7 +268,9 @@ __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ Spl
       float d[kS];
       long long N = 0;
       if (j < a.h_out && k < a.h_k) {
-        const unsigned long long x = operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j, a.trans);
+        const unsigned long long x =
+            (nt > 1 && a.vsum) ? a.vsum[((int64_t)p * a.h_k + k) * a.h_out + j]
+                               : operand_sum(a.src, a.ld, a.rows, a.cols, a.h_r, a.h_c, terms, nt, k, j, a.trans);
         N = scaled_rint(x, ecol[cc]);
       }
       digits_of(N, d);
@@ -700,6 +711,66 @@ __global__ void __launch_bounds__(256) oz_recombine_scatter(const __grid_constan
   }
 }
 
+// Up to two levels (at most 16 C blocks): one thread per local position (i, j) of the
+// blocks, holding that position of every C block in registers.  Each product's M_r is
+// recombined once (its seven group sums read once) and added into each of its target
+// blocks; the products run in table order, so every C element receives its additions
+// in exactly the order of oz_recombine_scatter, which reads each product's group sums
+// once per target instead.
+template <int NBLK>
+__global__ void __launch_bounds__(256) oz_recombine_local(const __grid_constant__ RecombineArgs a) {
+  const int Pn = 1 << a.levels;
+  const int64_t positions = a.hm * a.hn;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < positions;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / a.hn, j = e - (e / a.hn) * a.hn;
+    double c[NBLK];
+    unsigned valid = 0;
+#pragma unroll
+    for (int q = 0; q < NBLK; ++q) {
+      c[q] = 0.0;
+      if (q < Pn * Pn) {
+        const int64_t gr = (int64_t)(q / Pn) * a.hm + i, gc = (int64_t)(q % Pn) * a.hn + j;
+        if (gr < a.m && gc < a.n) {
+          valid |= 1u << q;
+          c[q] = a.C[gr * a.ldc + gc];
+        }
+      }
+    }
+    if (valid) {
+      for (int r = 0; r < a.P; ++r) {
+        const int row = a.plan_off + r;
+        const int nc = c_oz_plans.nc[row];
+        unsigned hit = 0;
+        for (int t = 0; t < nc; ++t) {
+          const uint8_t code = c_oz_plans.tc[row][t];
+          hit |= 1u << (term_bi(code) * Pn + term_bj(code));
+        }
+        if (!(hit & valid)) continue;
+        long long th;
+        unsigned long long tl;
+        group_total(a, r, i, j, &th, &tl);
+        const double M = round_i128(th, tl, a.e[(int64_t)r * a.h_mp + i] + a.f[(int64_t)r * a.h_np + j] - kB * (kS + 1));
+        const double aM = a.alpha == 1.0 ? M : a.alpha * M;  // no FP64 multiply for alpha = 1
+        for (int t = 0; t < nc; ++t) {
+          const uint8_t code = c_oz_plans.tc[row][t];
+          const int qq = term_bi(code) * Pn + term_bj(code);
+#pragma unroll
+          for (int q = 0; q < NBLK; ++q)
+            if (q == qq) c[q] = term_neg(code) ? c[q] - aM : c[q] + aM;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NBLK; ++q) {
+        if ((valid >> q) & 1u) {
+          const int64_t gr = (int64_t)(q / Pn) * a.hm + i, gc = (int64_t)(q % Pn) * a.hn + j;
+          a.C[gr * a.ldc + gc] = c[q];
+        }
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host side
 
 PFN_cuTensorMapEncodeTiled_v12000 g_oz_encode = nullptr;
@@ -753,8 +824,10 @@ int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
   const int64_t hmp = round_up(block_edge(m, levels), kTM), hnp = round_up(block_edge(n, levels), kTN),
                 hkp = round_up(block_edge(k, levels), kTK);
   const int64_t nseg = plan_segments(P * (hmp / kTM) * (hnp / kTN), hkp / kTK, std::max(device_sm_count(), 1));
+  const int64_t hk = block_edge(k, levels), hn = block_edge(n, levels);
+  const int64_t vsum = levels > 0 ? P * hk * hn * 8 + 256 : 0;  // B operand sums kept between the two B passes
   return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + nseg * kGroups * P * hmp * hnp * 4 + P * hnp * 8 +
-         4096;
+         vsum + 4096;
 }
 
 double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels) {
@@ -816,11 +889,15 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   const int nseg = plan_segments((int64_t)P * (hmp / kTM) * (hnp / kTN), hkp / kTK, sms);
   int* G = (int*)w;                                            w += (size_t)nseg * kGroups * P * hmp * hnp * 4;
   unsigned long long* colmax = (unsigned long long*)w;  // [P][h_np] magnitude bits
+  w += (size_t)P * hnp * 8;
+  w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+  unsigned long long* vsum = levels > 0 ? (unsigned long long*)w : nullptr;  // [P][h_k][h_n]
 
   SplitArgs sa;
   sa.src = A; sa.ld = lda; sa.rows = m; sa.cols = k; sa.h_r = hm; sa.h_c = hk;
   sa.h_out = hm; sa.h_outp = hmp; sa.h_k = hk; sa.h_kp = hkp;
   sa.plan_off = kPlanOffset[levels]; sa.slices = DX; sa.exps = ex; sa.trans = trans_a;
+  sa.vsum = nullptr;
   const size_t row_smem = (size_t)hk * sizeof(double);
   if (row_smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)oz_split_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -836,6 +913,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   sb.src = B; sb.ld = ldb; sb.rows = k; sb.cols = n; sb.h_r = hk; sb.h_c = hn;
   sb.h_out = hn; sb.h_outp = hnp; sb.h_k = hk; sb.h_kp = hkp;
   sb.plan_off = kPlanOffset[levels]; sb.slices = DV; sb.exps = fx; sb.trans = trans_b;
+  sb.vsum = vsum;
   e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)P * hnp, stream);
   if (e != cudaSuccess) return e;
   oz_colmax<<<dim3((unsigned)(hnp / 64), (unsigned)((hk + kColMaxRows - 1) / kColMaxRows), (unsigned)P), 256, 0,
@@ -889,8 +967,17 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
     ra.first[Pn * Pn] = n_upd;
   }
   const int threads = 256;
-  const int64_t blocks = std::min<int64_t>(m, (int64_t)sms * 8);
-  oz_recombine_scatter<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, stream>>>(ra);
+  if (levels <= 2) {
+    const int64_t positions = hm * hn;
+    const int64_t blocks = std::min<int64_t>((positions + threads - 1) / threads, (int64_t)sms * 32);
+    const unsigned grid = (unsigned)std::max<int64_t>(blocks, 1);
+    if (levels == 0) oz_recombine_local<1><<<grid, threads, 0, stream>>>(ra);
+    else if (levels == 1) oz_recombine_local<4><<<grid, threads, 0, stream>>>(ra);
+    else oz_recombine_local<16><<<grid, threads, 0, stream>>>(ra);
+  } else {
+    const int64_t blocks = std::min<int64_t>(m, (int64_t)sms * 8);
+    oz_recombine_scatter<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, stream>>>(ra);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess && stage_events) e = cudaEventRecord(stage_events[3], stream);
   return e;

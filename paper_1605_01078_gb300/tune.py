@@ -378,6 +378,9 @@ def main(argv=None) -> int:
     ap.add_argument("--train-skip", type=int, default=0,
                     help="skip the first N FP64 training shapes (already timed), time the rest of --train")
     ap.add_argument("--oz-train-skip", type=int, default=0, help="the same for the split-precision training shapes")
+    ap.add_argument("--ship", default=None,
+                    help="also write the trained network in the shipped format (data/selector_gb300.json): "
+                         "parameters, the held-out regrets, and the dtypes where it beat the method without it")
     ap.add_argument("--heldout-seed", type=int, default=2)
     ap.add_argument("--oz-heldout-seed", type=int, default=4)
     a = ap.parse_args(argv)
@@ -432,6 +435,25 @@ def main(argv=None) -> int:
         json.dump([float(v) for v in params], fh)
     with open(os.path.join(a.out, "selector_summary.json"), "w") as fh:
         json.dump(summary, fh, indent=1)
+    if a.ship:
+        use = {}
+        regrets = {}
+        for name, d in (("f64", f64), ("oz_bf16", oz)):
+            r_m, r_w = summary[name]["mlp"]["mean"], summary[name]["without_network"]["mean"]
+            use[str(d)] = bool(r_m is not None and r_w is not None and r_m < r_w)
+            regrets[name] = {"mlp": r_m, "without_network": r_w, "shapes": summary[name]["shapes"]}
+        use.setdefault("1", False)
+        meta = {"description": (
+                    f"Variant-selector MLP ({B.SELECTOR_INPUTS}-64-64-{NC}, FP32) predicting a correction to the "
+                    f"analytic model's log2 seconds, trained with the library's kernels ({a.steps} full-batch Adam "
+                    f"steps, lr {a.lr}) on {summary['timings_train']} timings of {summary['shapes_train']} shapes "
+                    f"(m, n, k log-uniform in [{a.lo}, {a.hi}]) measured on one GB300; held out: "
+                    f"{regrets['f64']['shapes']} FP64 and {regrets['oz_bf16']['shapes']} split-precision shapes. "
+                    "use_for_dtype: where its mean held-out regret is below the method without it."),
+                "use_for_dtype": use, "heldout_regret_mean": regrets,
+                "params": [float(v) for v in params]}
+        with open(a.ship, "w") as fh:
+            json.dump(meta, fh)
     print(json.dumps({k: summary[k] for k in ("f64", "oz_bf16")}, indent=1))
     return 0
 
