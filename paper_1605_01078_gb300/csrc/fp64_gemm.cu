@@ -105,7 +105,9 @@ struct alignas(128) ProbDesc {
   int64_t a_rows, a_cols, b_rows, b_cols, c_rows, c_cols;
   int64_t hm, hn, hk;
   int64_t iter_begin;  // first iteration of this problem in the stream-K space
-  int64_t unit_begin;  // batched: index of this problem's first work unit
+  int64_t claim_begin;  // batched: index of this problem's first claim
+  int64_t units;        // batched: work units of this problem
+  int32_t units_per_claim;  // batched: whole units per claim (short units go several to a claim)
   int32_t plan_row;    // table row of the first product of this problem
   int32_t nprod;
   int32_t m_target;
@@ -125,7 +127,7 @@ struct KArgs {
   int nprob;
   int sched;
   int64_t total;           // stream-K: iterations of all problems; owner: tile positions
-  int64_t nchunks;         // batched: work units to claim (one claim = one whole unit)
+  int64_t nchunks;         // batched: claims (each one or more whole units of one problem)
   int64_t dp_rounds;       // single stream-K launch: rounds of whole units before the split tail
 };
 
@@ -226,16 +228,19 @@ __device__ Cursor range_cursor(const KArgs& a, int64_t id) {
     int64_t beg, end;
     int p = 0;
     if constexpr (BATCHED) {
-      // Claim `id` is one whole unit: problem p is the last whose first unit is <= id.
+      // Claim `id` holds whole units of one problem: p is the last problem whose first
+      // claim is <= id.
       int lo = 0, hi = a.nprob - 1;
       while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
-        if (a.descs[mid].unit_begin <= id) lo = mid; else hi = mid - 1;
+        if (a.descs[mid].claim_begin <= id) lo = mid; else hi = mid - 1;
       }
       p = lo;
       const ProbDesc& dp = a.descs[p];
-      beg = dp.iter_begin + (id - dp.unit_begin) * dp.ksteps;
-      end = beg + dp.ksteps;
+      const int64_t u0 = (id - dp.claim_begin) * dp.units_per_claim;
+      const int64_t u1 = u0 + dp.units_per_claim < dp.units ? u0 + dp.units_per_claim : dp.units;
+      beg = dp.iter_begin + u0 * dp.ksteps;
+      end = dp.iter_begin + u1 * dp.ksteps;
     } else {
       // Claims 0 .. dp_rounds - 1: whole units, round-robin over the blocks, so the
       // blocks of one round work on neighbouring tiles of the same product at the same
@@ -952,6 +957,7 @@ namespace {
 // descriptors -- TMA tensor maps encoded on the host included -- into the device
 // array the persistent kernel reads.
 constexpr int kDescPerExpand = (32000 - 64) / (int)sizeof(ProbDesc);
+constexpr int kClaimSteps = 32;
 struct ExpandArgs {
   ProbDesc* out;
   unsigned long long* counter;  // cleared when not null
@@ -1020,13 +1026,17 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   // tile, so the blocks that run at the same time work on neighbouring tiles of one
   // product at about the same k and share operand tiles in the L2.
   std::stable_sort(descs.begin(), descs.end(), [](const ProbDesc& x, const ProbDesc& y) { return x.ksteps > y.ksteps; });
-  int64_t total = 0, units = 0;
+  // A claim takes whole units of one problem, enough for at least kClaimSteps k-steps, so
+  // that the claim hand-over (a global atomic and a handshake between the producers) is
+  // paid rarely on problems with short units (three levels of a small product).
+  int64_t total = 0, claims = 0;
   for (ProbDesc& d : descs) {
     d.iter_begin = total;
-    d.unit_begin = units;
-    const int64_t nu = (int64_t)d.nprod * d.tiles_m * d.tiles_n;
-    units += nu;
-    total += nu * d.ksteps;
+    d.claim_begin = claims;
+    d.units = (int64_t)d.nprod * d.tiles_m * d.tiles_n;
+    d.units_per_claim = std::max(1, kClaimSteps / d.ksteps);
+    claims += (d.units + d.units_per_claim - 1) / d.units_per_claim;
+    total += d.units * d.ksteps;
   }
   if (descs.empty()) return cudaSuccess;
   ProbDesc* dev = (ProbDesc*)scratch;
@@ -1050,7 +1060,7 @@ cudaError_t launch_fp64_batched(const Fp64Launch* probs, int count, void* scratc
   args.nprob = (int)descs.size();
   args.sched = kSchedStreamK;
   args.total = total;
-  args.nchunks = units;  // blocks claim whole units until none are left
+  args.nchunks = claims;  // blocks claim until none are left
   const int64_t grid = std::min<int64_t>(sms, args.nchunks);
   void* kargs[] = {&args};
   return cudaLaunchKernel(pick_kernel(cls, true, tile), dim3((unsigned)grid), dim3(kThreads), kargs,

@@ -26,7 +26,8 @@
 //
 // GB300 notes.  FP64 arithmetic runs at about 2 lanes per clock per SM here, so the
 // split and recombine steps use integer arithmetic for everything but the operand sums
-// and the final C additions; the products run on the BF16 tensor cores (tcgen05.mma
+// and the final C additions (digits are converted from 32-bit integers: a 64-bit
+// integer conversion would run on the FP64 pipe); the products run on the BF16 tensor cores (tcgen05.mma
 // kind::f16, 128x256 tiles, accumulators in tensor memory) fed by TMA with 128-byte
 // swizzle.  The 128x256 tile moves 3/4 of the operand bytes per flop of a 128x128 one
 // (the 128x128 kernel was held by L2-to-SM bandwidth); int32 chunk sums keep its
@@ -42,7 +43,6 @@
 #include <cstring>
 #include <mutex>
 
-#include "int_fadd.h"
 #include "internal.h"
 
 namespace sgb {
@@ -108,9 +108,9 @@ __device__ __forceinline__ void digits_of(long long N, float* d) {
     const int q = kB * (kS - s);
     const long long v = (N + (1LL << (q - 1))) >> q;
     N -= v * (1LL << q);
-    d[s - 1] = (float)v;
+    d[s - 1] = (float)(int)v;  // |v| <= 128: a 32-bit conversion (a 64-bit one runs on the FP64 pipe)
   }
-  d[kS - 1] = (float)N;
+  d[kS - 1] = (float)(int)N;
 }
 
 __device__ __forceinline__ unsigned long long mag_bits(unsigned long long bits) {
@@ -118,22 +118,23 @@ __device__ __forceinline__ unsigned long long mag_bits(unsigned long long bits) 
 }
 
 // Bits of the operand sum x = sum_t sign_t * src[block_t](r, c), masked to the source
-// extent, formed with the integer-pipe addition (no floating-point instruction).
+// extent, added left to right.  The split kernels leave the FP64 pipe idle otherwise,
+// so the additions use it (DADD); the integer pipe carries the digit extraction.
 __device__ __forceinline__ unsigned long long operand_sum(const double* src, int64_t ld, int64_t rows,
                                                           int64_t cols, int64_t h_r, int64_t h_c,
                                                           const uint8_t* terms, int nterms, int64_t r, int64_t c,
                                                           int trans) {
   const unsigned long long* s64 = reinterpret_cast<const unsigned long long*>(src);
-  unsigned long long v = 0;
+  double v = 0.0;
   for (int t = 0; t < nterms; ++t) {
     const uint8_t code = terms[t];
     const int64_t gr = (int64_t)term_bi(code) * h_r + r, gc = (int64_t)term_bj(code) * h_c + c;
     unsigned long long x = 0;
     if (r < h_r && c < h_c && gr < rows && gc < cols) x = trans ? s64[gc * ld + gr] : s64[gr * ld + gc];
     x ^= (unsigned long long)term_neg(code) << 63;
-    v = t == 0 ? x : int_fadd_bits(v, x);
+    v = t == 0 ? __longlong_as_double((long long)x) : __dadd_rn(v, __longlong_as_double((long long)x));
   }
-  return v;
+  return (unsigned long long)__double_as_longlong(v);
 }
 
 // ---------------------------------------------------------------- split kernels
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(256) oz_recombine_scatter(const __grid_constan
 // in exactly the order of oz_recombine_scatter, which reads each product's group sums
 // once per target instead.
 template <int NBLK>
-__global__ void __launch_bounds__(256) oz_recombine_local(const __grid_constant__ RecombineArgs a) {
+__global__ void __launch_bounds__(256, 3) oz_recombine_local(const __grid_constant__ RecombineArgs a) {
   const int Pn = 1 << a.levels;
   const int64_t positions = a.hm * a.hn;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < positions;
