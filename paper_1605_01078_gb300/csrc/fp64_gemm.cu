@@ -405,61 +405,77 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
 
     auto issue = [&](const Cursor& c, int slot) {
       const ProbDesc& d = desc_of<BATCHED>(a, c.p);
+      // The descriptor's fields in registers: in a batched launch it lives in global
+      // memory, and every copy instruction below (asm with a memory clobber) would
+      // otherwise make the compiler load the fields again.
+      const int64_t hm = d.hm, hn = d.hn, hk = d.hk;
       const int row = d.plan_row + c.r;
       const int na = min((int)c_plans.na[row], MAXT), nb = min((int)c_plans.nb[row], MAXT);
-      const int tm = c.t / d.tiles_n, tn = c.t - (c.t / d.tiles_n) * d.tiles_n;
+      const int tiles_n = d.tiles_n;
+      const int tm = c.t / tiles_n, tn = c.t - (c.t / tiles_n) * tiles_n;
+      const int trans_a = d.trans_a, trans_b = d.trans_b;
       double* ra = rawA + slot * S::kRawA;
       double* rb = rawB + slot * S::kRawB;
       if (d.use_tma) {
         if (pt == 0) {
+          const CUtensorMap* tmA = &d.tmA;
+          const CUtensorMap* tmB = &d.tmB;
           mbar_arrive_expect_tx(&raw_full[slot], (uint32_t)((na * BM * BK + nb * BK * BN) * sizeof(double)));
           for (int t = 0; t < na; ++t) {
             const uint8_t code = c_plans.ta[row][t];
-            const int rr = (int)(term_bi(code) * d.hm + (int64_t)tm * BM), kc = (int)(term_bj(code) * d.hk + (int64_t)c.ks * BK);
+            const int rr = (int)(term_bi(code) * hm + (int64_t)tm * BM), kc = (int)(term_bj(code) * hk + (int64_t)c.ks * BK);
             // A box [BM][BK] (row, k), or for A^T the stored box [BK][BM] (k, row)
-            if (d.trans_a) tma_load_2d(ra + t * BM * BK, &d.tmA, rr, kc, &raw_full[slot]);
-            else tma_load_2d(ra + t * BM * BK, &d.tmA, kc, rr, &raw_full[slot]);
+            if (trans_a) tma_load_2d(ra + t * BM * BK, tmA, rr, kc, &raw_full[slot]);
+            else tma_load_2d(ra + t * BM * BK, tmA, kc, rr, &raw_full[slot]);
           }
           for (int t = 0; t < nb; ++t) {
             const uint8_t code = c_plans.tb[row][t];
-            const int kr = (int)(term_bi(code) * d.hk + (int64_t)c.ks * BK), cc = (int)(term_bj(code) * d.hn + (int64_t)tn * BN);
+            const int kr = (int)(term_bi(code) * hk + (int64_t)c.ks * BK), cc = (int)(term_bj(code) * hn + (int64_t)tn * BN);
             // B box [BK][BN] (k, col), or for B^T the stored box [BN][BK] (col, k)
-            if (d.trans_b) tma_load_2d(rb + t * BK * BN, &d.tmB, kr, cc, &raw_full[slot]);
-            else tma_load_2d(rb + t * BK * BN, &d.tmB, cc, kr, &raw_full[slot]);
+            if (trans_b) tma_load_2d(rb + t * BK * BN, tmB, kr, cc, &raw_full[slot]);
+            else tma_load_2d(rb + t * BK * BN, tmB, cc, kr, &raw_full[slot]);
           }
         } else {
           mbar_arrive(&raw_full[slot]);
         }
       } else {
+        {
+        const double* A = d.A;
+        const int64_t lda = d.lda, a_rows = d.a_rows, a_cols = d.a_cols;
         for (int t = 0; t < na; ++t) {
           const uint8_t code = c_plans.ta[row][t];
-          const int64_t r0 = (int64_t)term_bi(code) * d.hm, c0 = (int64_t)term_bj(code) * d.hk;
+          const int64_t r0 = (int64_t)term_bi(code) * hm, c0 = (int64_t)term_bj(code) * hk;
 #pragma unroll
           for (int q = 0; q < (BM * BK) / kProducers; ++q) {
             const int e = pt + q * kProducers;
             // raw layout [BM][BK], or [BK][BM] for A^T (the layout of the TMA box)
-            const int i = d.trans_a ? e % BM : e / BK, kk = d.trans_a ? e / BM : e % BK;
+            const int i = trans_a ? e % BM : e / BK, kk = trans_a ? e / BM : e % BK;
             const int64_t li = (int64_t)tm * BM + i, lk = (int64_t)c.ks * BK + kk;
             const int64_t gr = r0 + li, gc = c0 + lk;  // element (gr, gc) of op(A)
-            const bool ok = li < d.hm && lk < d.hk && gr < d.a_rows && gc < d.a_cols;
-            const double* src = d.trans_a ? d.A + gc * d.lda + gr : d.A + gr * d.lda + gc;
-            cp_async8(ra + t * BM * BK + e, ok ? src : d.A, ok ? 8 : 0);
+            const bool ok = li < hm && lk < hk && gr < a_rows && gc < a_cols;
+            const double* src = trans_a ? A + gc * lda + gr : A + gr * lda + gc;
+            cp_async8(ra + t * BM * BK + e, ok ? src : A, ok ? 8 : 0);
           }
         }
+        }
+        {
+        const double* B = d.B;
+        const int64_t ldb = d.ldb, b_rows = d.b_rows, b_cols = d.b_cols;
         for (int t = 0; t < nb; ++t) {
           const uint8_t code = c_plans.tb[row][t];
-          const int64_t r0 = (int64_t)term_bi(code) * d.hk, c0 = (int64_t)term_bj(code) * d.hn;
+          const int64_t r0 = (int64_t)term_bi(code) * hk, c0 = (int64_t)term_bj(code) * hn;
 #pragma unroll
           for (int q = 0; q < (BN * BK) / kProducers; ++q) {
             const int e = pt + q * kProducers;
             // raw layout [BK][BN], or [BN][BK] for B^T
-            const int kk = d.trans_b ? e % BK : e / BN, jj = d.trans_b ? e / BK : e % BN;
+            const int kk = trans_b ? e % BK : e / BN, jj = trans_b ? e / BK : e % BN;
             const int64_t lk = (int64_t)c.ks * BK + kk, lj = (int64_t)tn * BN + jj;
             const int64_t gr = r0 + lk, gc = c0 + lj;  // element (gr, gc) of op(B)
-            const bool ok = lk < d.hk && lj < d.hn && gr < d.b_rows && gc < d.b_cols;
-            const double* src = d.trans_b ? d.B + gc * d.ldb + gr : d.B + gr * d.ldb + gc;
-            cp_async8(rb + t * BK * BN + e, ok ? src : d.B, ok ? 8 : 0);
+            const bool ok = lk < hk && lj < hn && gr < b_rows && gc < b_cols;
+            const double* src = trans_b ? B + gc * ldb + gr : B + gr * ldb + gc;
+            cp_async8(rb + t * BK * BN + e, ok ? src : B, ok ? 8 : 0);
           }
+        }
         }
         cp_async_mbar_arrive(&raw_full[slot]);
       }
@@ -503,6 +519,8 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       const ProbDesc& d = desc_of<BATCHED>(a, cur.p);
       const int row = d.plan_row + cur.r;
       const int na = min((int)c_plans.na[row], MAXT), nb = min((int)c_plans.nb[row], MAXT);
+      const int64_t dhk = d.hk;
+      const int dtrans_a = d.trans_a, dtrans_b = d.trans_b;
       // The sums run on binary64 bit patterns with the integer-pipe addition: no
       // floating-point value (or instruction) appears in the producer's path.
       const uint64_t* ra = reinterpret_cast<const uint64_t*>(rawA + slot * S::kRawA);
@@ -522,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       {
         uint64_t v[EPT];
         const uint64_t s0 = (uint64_t)term_neg(c_plans.ta[row][0]) << 63;
-        if (!d.trans_a) {
+        if (!dtrans_a) {
           const ulonglong2* r0 = reinterpret_cast<const ulonglong2*>(ra + pr * BK + koff);
 #pragma unroll
           for (int h = 0; h < EPT / 2; ++h) {
@@ -551,12 +569,12 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
           }
         }
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) sa[(koff + i) * BM + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
+        for (int i = 0; i < EPT; ++i) sa[(koff + i) * BM + pr] = (k0 + koff + i < dhk) ? v[i] : 0;
       }
       {
         uint64_t v[EPT];
         const uint64_t s0 = (uint64_t)term_neg(c_plans.tb[row][0]) << 63;
-        if (!d.trans_b) {
+        if (!dtrans_b) {
 #pragma unroll
           for (int i = 0; i < EPT; ++i) v[i] = rb[(koff + i) * BN + pr] ^ s0;
           for (int t = 1; t < nb; ++t) {
@@ -585,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
           }
         }
 #pragma unroll
-        for (int i = 0; i < EPT; ++i) sb[(koff + i) * BN + pr] = (k0 + koff + i < d.hk) ? v[i] : 0;
+        for (int i = 0; i < EPT; ++i) sb[(koff + i) * BN + pr] = (k0 + koff + i < dhk) ? v[i] : 0;
       }
       if (pt == 0) meta[q] = StepMeta{cur.p, cur.r, cur.t, step_flags<BATCHED>(a, cur)};
       mbar_arrive(&sum_full[q]);
@@ -706,19 +724,28 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
           const int64_t row0 = (int64_t)term_bi(code) * d.hm + (int64_t)tm * BM;
           const int64_t col0 = (int64_t)term_bj(code) * d.hn + (int64_t)tn * BN;
           const int64_t row_lim = min(d.hm - (int64_t)tm * BM, d.c_rows - row0);
-          const int64_t col_lim = min(d.hn - (int64_t)tn * BN, d.c_cols - col0);
+          const int col_lim = (int)min(d.hn - (int64_t)tn * BN, d.c_cols - col0);
+          // Row pointers and the triangle bound in registers (a batched launch reads
+          // its descriptor from global memory, and each atomic below would otherwise
+          // make the compiler load the fields again).  The triangle test compares the
+          // tile-local column with gi - col0 (lower: j <= i, upper: j >= i).
+          const int64_t ldc = d.ldc;
+          double* const c_r0 = d.C + (row0 + rr0) * ldc + col0;
+          double* const c_r1 = d.C + (row0 + rr1) * ldc + col0;
+          const int tri = d.tri;
+          const int64_t diag0 = row0 + rr0 - col0, diag1 = row0 + rr1 - col0;  // gi - col0 of the two rows
+          const bool ok0 = rr0 < row_lim, ok1 = rr1 < row_lim;
 #pragma unroll
           for (int q = 0; q < (2 * BN) / 32; ++q) {
             const int e = lane + 32 * q;
             const int h = e / BN, col = e - (e / BN) * BN;
-            const int rr = h ? rr1 : rr0;
-            const int64_t gi = row0 + rr, gj = col0 + col;
-            const bool in_tri = d.tri == 0 || (d.tri == 1 ? gj <= gi : gj >= gi);
-            if (rr < row_lim && col < col_lim && in_tri)
+            const int64_t dg = h ? diag1 : diag0;
+            const bool in_tri = tri == 0 || (tri == 1 ? col <= dg : col >= dg);
+            if ((h ? ok1 : ok0) && col < col_lim && in_tri)
               // red.global.add.f64, performed in the L2 (off the FP64 pipe).  Each C
               // element of a tile is always updated by the same thread, in product
               // order, so one owner per tile gives a deterministic result.
-              atomicAdd(d.C + (row0 + rr) * d.ldc + col0 + col, flip_sign(stage[e], neg));
+              atomicAdd((h ? c_r1 : c_r0) + col, flip_sign(stage[e], neg));
           }
         }
         __syncwarp();
