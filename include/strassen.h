@@ -71,7 +71,9 @@ typedef enum {
   STRASSEN_ABC = 0,   /* sums fused into operand staging, M_r scattered into C in the epilogue */
   STRASSEN_AB = 1,    /* sums fused into operand staging, M_r to a temporary, then C updates */
   STRASSEN_NAIVE = 2, /* operand-sum temporaries, classical GEMM into M_r, then C updates */
-  STRASSEN_AUTO = 3   /* chosen by strassen_select() */
+  STRASSEN_AUTO = 3,  /* chosen by strassen_select() */
+  STRASSEN_HYBRID = 4 /* AB at the outermost level over ABC for the levels below it (levels >= 2;
+                         at one level it is AB): see strassen_gemm */
 } strassen_variant;
 
 /* Arithmetic of the products. */
@@ -111,7 +113,7 @@ typedef enum {
  *   B, ldb        device pointer and row stride of B, ldb >= max(n, 1).
  *   C, ldc        device pointer and row stride of C, ldc >= max(n, 1); read and written.
  *   levels        -1 (auto), 0, 1, 2 or 3.
- *   variant       STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE or STRASSEN_AUTO.
+ *   variant       STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE, STRASSEN_HYBRID or STRASSEN_AUTO.
  *   dtype         STRASSEN_F64 or one of the split-precision dtypes.
  *   stream        the CUDA stream the work is ordered on.
  *
@@ -121,6 +123,16 @@ typedef enum {
  * the rounding order (not the mathematical result) can vary from run to run;
  * strassen_dgemm_ex with STRASSEN_FLAG_DETERMINISTIC makes every C tile owned by one
  * thread block, which fixes the order (at some cost in load balance).
+ *
+ * Hybrid plans (Eq. 4 applied with different variants at different levels): with
+ * STRASSEN_HYBRID and L >= 2 levels the outermost level is AB and the L-1 levels below
+ * it are ABC: for each of the 7 outer products a, one launch runs its 7^(L-1) inner
+ * products with fused operand sums (the L-level table's terms) and scatters them, in
+ * the epilogue, into the quadrants of a temporary M_a of (2^(L-1) ceil(m/2^L)) x
+ * (2^(L-1) ceil(n/2^L)) doubles with the inner table's coefficients; a separate pass
+ * then adds gamma M_a into the C blocks of outer product a.  (The other mix, ABC over
+ * AB, is the L-level AB variant itself: its temporaries are scattered with the
+ * composite coefficients.)  The temporary is stream-ordered, as for AB.
  *
  * Accuracy: each FP64 partial product is accumulated over at most 256 of k (128 at
  * three levels) in registers and then added into C (or M), so no sequential sum is

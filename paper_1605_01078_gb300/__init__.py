@@ -14,7 +14,7 @@ All arithmetic runs in the library's CUDA kernels; a missing library is an error
 from __future__ import annotations
 
 from . import _binding
-from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  # noqa: F401
+from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64, STRASSEN_HYBRID,  # noqa: F401
                        STRASSEN_F64_OZ_BF16, STRASSEN_F64_OZ_INT8, STRASSEN_FLAG_DETERMINISTIC, STRASSEN_NAIVE,
                        StrassenError,
                        classical_gemm, strassen_gemm, strassen_gemm_ab_noalloc, strassen_gemm_batched,
@@ -28,7 +28,8 @@ from ._binding import (STRASSEN_AB, STRASSEN_ABC, STRASSEN_AUTO, STRASSEN_F64,  
                        strassen_workspace_size, strassen_profile_split_precision,
                        strassen_selector_candidate, strassen_selector_features)
 
-VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO}
+VARIANTS = {"ABC": STRASSEN_ABC, "AB": STRASSEN_AB, "NAIVE": STRASSEN_NAIVE, "AUTO": STRASSEN_AUTO,
+            "HYBRID": STRASSEN_HYBRID}
 DTYPES = {"f64": STRASSEN_F64, "oz_int8": STRASSEN_F64_OZ_INT8, "oz_bf16": STRASSEN_F64_OZ_BF16}
 
 

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libstrassen_gb300.so")
 
 # enums of strassen.h
-STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE, STRASSEN_AUTO = 0, 1, 2, 3
+STRASSEN_ABC, STRASSEN_AB, STRASSEN_NAIVE, STRASSEN_AUTO, STRASSEN_HYBRID = 0, 1, 2, 3, 4
 STRASSEN_F64, STRASSEN_F64_OZ_INT8, STRASSEN_F64_OZ_BF16 = 0, 1, 2
 STRASSEN_FLAG_DETERMINISTIC = 1
 MAX_LEVELS, MAX_TERMS = 3, 8   # STRASSEN_MAX_LEVELS, STRASSEN_MAX_TERMS

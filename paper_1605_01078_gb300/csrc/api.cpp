@@ -142,6 +142,45 @@ int run_ab(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const 
   return STRASSEN_OK;
 }
 
+// Hybrid plan: AB at the outermost level, ABC below it.  For each outer product a the
+// launch runs rows [7^(L-1) a, 7^(L-1) (a + 1)) of the L-level table (operand sums fused,
+// as in ABC) and scatters them with the (L-1)-level table's coefficients into the
+// temporary M_a (outer blocks of 2^(L-1) h); then M_a is added into C with the outer
+// product's coefficients of Figure 1.
+int run_hybrid(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double* C, int64_t ldc, int levels, cudaStream_t s, int tile, const Op& op = Op()) {
+  if (levels < 2) return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
+  Plan outer;
+  if (!make_plan(1, &outer)) return STRASSEN_ERR_LEVELS;
+  const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels);
+  const int64_t sub = (int64_t)1 << (levels - 1);
+  const int64_t om = sub * hm, on = sub * hn;  // the outer blocks of the L-level partition
+  Workspace ws;
+  ws.s = s;
+  if (cudaMallocAsync(&ws.p, sizeof(double) * om * on, s) != cudaSuccess) {
+    cudaGetLastError();
+    ws.p = nullptr;
+    return STRASSEN_ERR_ALLOC;
+  }
+  double* M = (double*)ws.p;
+  const int inner = kPlanCount[levels - 1];
+  for (int a = 0; a < 7; ++a) {
+    Fp64Launch L = make_launch(m, n, k, A, lda, B, ldb, M, on, levels);
+    L.c_rows = om; L.c_cols = on;
+    L.prod_begin = a * inner; L.nprod = inner;
+    L.inner_targets = 1;
+    L.epi = kEpiStore;
+    L.tile = tile;
+    L.trans_a = op.ta; L.trans_b = op.tb;  // alpha is applied by the C updates
+    choose_fp64_schedule(&L, op.det);
+    if (cudaMemsetAsync(M, 0, sizeof(double) * om * on, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
+    if (launch_fp64(L, s) != cudaSuccess) return STRASSEN_ERR_CUDA;
+    if (launch_combine(C, ldc, m, n, M, om, on, outer.tc[a], outer.nc[a], s, op.alpha) != cudaSuccess)
+      return STRASSEN_ERR_CUDA;
+  }
+  return STRASSEN_OK;
+}
+
 int run_naive(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
               int64_t ldb, double* C, int64_t ldc, int levels, cudaStream_t s, int tile, const Op& op = Op()) {
   Plan pl;
@@ -258,6 +297,7 @@ int run_product(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, c
     case STRASSEN_ABC: return run_abc(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
     case STRASSEN_AB: return run_ab(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
     case STRASSEN_NAIVE: return run_naive(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
+    case STRASSEN_HYBRID: return run_hybrid(m, n, k, A, lda, B, ldb, C, ldc, levels, s, tile, op);
     default: return STRASSEN_ERR_UNSUPPORTED;
   }
 }
@@ -349,7 +389,7 @@ int strassen_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
                   strassen_dtype dtype, strassen_stream_t stream) {
   try {
     if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
-    if ((int)variant < 0 || (int)variant > 3) return STRASSEN_ERR_UNSUPPORTED;
+    if ((int)variant < 0 || (int)variant > 4) return STRASSEN_ERR_UNSUPPORTED;
     if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
     const int chk = check_args(m, n, k, A, lda, B, ldb, C, ldc);
     if (chk < 0) return chk;
@@ -367,7 +407,7 @@ int strassen_dgemm_ex(int transa, int transb, int64_t m, int64_t n, int64_t k, d
     if (transa < 0 || transa > 1 || transb < 0 || transb > 1) return STRASSEN_ERR_ARG;
     if (flags & ~(unsigned)STRASSEN_FLAG_DETERMINISTIC) return STRASSEN_ERR_ARG;
     if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
-    if ((int)variant < 0 || (int)variant > 3) return STRASSEN_ERR_UNSUPPORTED;
+    if ((int)variant < 0 || (int)variant > 4) return STRASSEN_ERR_UNSUPPORTED;
     if ((int)dtype < 0 || (int)dtype > 2) return STRASSEN_ERR_UNSUPPORTED;
     Op op;
     op.ta = transa; op.tb = transb; op.alpha = alpha;
@@ -424,10 +464,11 @@ int strassen_gemm_batched(int count, const strassen_problem* probs, strassen_dty
     for (int i = 0; i < count; ++i) {
       const strassen_problem& p = probs[i];
       if (p.levels < -1 || p.levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
-      if ((int)p.variant < 0 || (int)p.variant > 3) return STRASSEN_ERR_UNSUPPORTED;
-      // The persistent launch runs the fused (ABC) form only: AB and Naive need their
-      // temporaries and separate passes per product.
-      if ((p.variant == STRASSEN_AB || p.variant == STRASSEN_NAIVE) && p.levels != 0)
+      if ((int)p.variant < 0 || (int)p.variant > 4) return STRASSEN_ERR_UNSUPPORTED;
+      // The persistent launch runs the fused (ABC) form only: AB, Naive and the hybrid
+      // plan need their temporaries and separate passes per product.
+      if ((p.variant == STRASSEN_AB || p.variant == STRASSEN_NAIVE || p.variant == STRASSEN_HYBRID) &&
+          p.levels != 0)
         return STRASSEN_ERR_UNSUPPORTED;
       const int chk = check_args(p.m, p.n, p.k, p.A, p.lda, p.B, p.ldb, p.C, p.ldc);
       if (chk < 0) return chk;
@@ -634,7 +675,7 @@ int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, str
                                 strassen_dtype dtype) {
   if (m < 0 || n < 0 || k < 0) return STRASSEN_ERR_DIM;
   if (levels < -1 || levels > kMaxLevels) return STRASSEN_ERR_LEVELS;
-  if ((int)variant < 0 || (int)variant > 3 || (int)dtype < 0 || (int)dtype > 2)
+  if ((int)variant < 0 || (int)variant > 4 || (int)dtype < 0 || (int)dtype > 2)
     return STRASSEN_ERR_UNSUPPORTED;
   if (m == 0 || n == 0 || k == 0) return 0;
   if (levels == -1 || variant == STRASSEN_AUTO) {
@@ -649,7 +690,11 @@ int64_t strassen_workspace_size(int64_t m, int64_t n, int64_t k, int levels, str
   if (dtype == STRASSEN_F64_OZ_BF16) return ozaki_workspace_bytes(m, n, k, levels);
   if (levels == 0 || variant == STRASSEN_ABC) return 0;
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
-  if (variant == STRASSEN_AB) return (int64_t)sizeof(double) * hm * hn;
+  if (variant == STRASSEN_AB || (variant == STRASSEN_HYBRID && levels < 2)) return (int64_t)sizeof(double) * hm * hn;
+  if (variant == STRASSEN_HYBRID) {
+    const int64_t sub = (int64_t)1 << (levels - 1);
+    return (int64_t)sizeof(double) * (sub * hm) * (sub * hn);
+  }
   return (int64_t)sizeof(double) * (hm * hk + hk * hn + hm * hn);
 }
 

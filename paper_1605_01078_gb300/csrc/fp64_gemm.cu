@@ -117,6 +117,9 @@ struct alignas(128) ProbDesc {
   int32_t flush_steps;       // k-steps per accumulation chunk (partial sums leave the registers)
   int32_t trans_a, trans_b;  // op(A) = A^T (A stored k x m), op(B) = B^T (B stored n x k)
   int32_t tri;               // level 0: 0 all of C, 1 only j <= i, 2 only j >= i (local to C)
+  int32_t target_row0;       // first table row of the launch's level (for inner targets)
+  int32_t inner_row0;        // inner targets: first row of the (L-1)-level table, else -1
+  int32_t inner_count;       // inner targets: 7^(L-1)
   double alpha;              // the product is scaled by alpha in the scatter
 };
 
@@ -688,7 +691,11 @@ __global__ void __launch_bounds__(kThreads, 1) fp64_strassen_kernel(const __grid
       // staging buffer, so that each warp issues coalesced atomics over whole tile rows
       // (and the register tile is not held twice).
       const ProbDesc& d = desc_of<BATCHED>(a, m.p);
-      const int row = d.plan_row + m.r;
+      // The C coefficients: the product's own row, or for the inner products of a
+      // hybrid plan the row of the (L-1)-level table it comes from (product index
+      // 7^(L-1) a + b of the L-level table is inner product b of outer product a).
+      const int row = d.inner_row0 < 0 ? d.plan_row + m.r
+                                       : d.inner_row0 + (d.plan_row + m.r - d.target_row0) % d.inner_count;
       const int nc = d.m_target ? 1 : (int)c_plans.nc[row];
       const int tm = m.t / d.tiles_n, tn = m.t - (m.t / d.tiles_n) * d.tiles_n;
       const int warp = tid >> 5, lane = tid & 31;
@@ -879,6 +886,9 @@ void fill_desc(const Fp64Launch& L, ProbDesc* d) {
   d->trans_a = L.trans_a;
   d->trans_b = L.trans_b;
   d->tri = L.levels == 0 ? L.tri : 0;
+  d->target_row0 = kPlanOffset[L.levels];
+  d->inner_row0 = (L.inner_targets && L.levels >= 2) ? kPlanOffset[L.levels - 1] : -1;
+  d->inner_count = L.levels >= 1 ? kPlanCount[L.levels - 1] : 1;
   d->alpha = L.alpha;
   d->flush_steps = accumulation_chunk_k(L.levels) / BK;
   // The innermost TMA coordinate is a block offset along k (A), n (B), m (A^T) or k

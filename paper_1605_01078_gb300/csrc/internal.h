@@ -64,6 +64,8 @@ struct Fp64Launch {
   int trans_a, trans_b;    // op(A) = A^T (A stored k x m, ld >= m); op(B) = B^T (stored n x k)
   double alpha;            // C += alpha * (product); 1 for the plain operation
   int tri;                 // level 0 only: 0 every element of C, 1 only j <= i, 2 only j >= i
+  int inner_targets;       // levels >= 2: scatter with the (levels-1)-level table's C coefficients
+                           // (the inner products of the hybrid plan), blocks of hm x hn in C
 };
 
 // Fills the fields common to a full-operand launch.

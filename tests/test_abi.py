@@ -81,8 +81,13 @@ def test_workspace_sizes():
     assert f(1024, 1024, 1024, 0, sg.STRASSEN_AB, 0) == 0
     assert f(1024, 1024, 1024, 1, sg.STRASSEN_AB, 0) == 8 * 512 * 512
     assert f(1000, 998, 7, 2, sg.STRASSEN_NAIVE, 0) == 8 * (250 * 2 + 2 * 250 + 250 * 250)
+    # hybrid: the outer blocks of the L-level partition, 2^(L-1) ceil(d / 2^L)
+    assert f(1000, 998, 7, 2, sg.STRASSEN_HYBRID, 0) == 8 * (2 * 250) * (2 * 250)
+    assert f(1001, 999, 64, 3, sg.STRASSEN_HYBRID, 0) == 8 * (4 * 126) * (4 * 125)
+    assert f(1024, 1024, 1024, 1, sg.STRASSEN_HYBRID, 0) == 8 * 512 * 512
     assert f(-1, 4, 4, 1, 0, 0) == -1
     assert f(4, 4, 4, 5, 0, 0) == -4
+    assert f(4, 4, 4, 1, 5, 0) == -5
 
 
 def test_status_strings():

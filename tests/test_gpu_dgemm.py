@@ -44,7 +44,7 @@ def run(A, B, C, alpha, beta, ta, tb, levels, variant, dtype="f64"):
 
 @pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
 @pytest.mark.parametrize("levels,variant", [(0, "ABC"), (1, "ABC"), (1, "AB"), (1, "NAIVE"), (2, "ABC"),
-                                            (2, "AB"), (2, "NAIVE"), (3, "ABC")])
+                                            (2, "AB"), (2, "NAIVE"), (3, "ABC"), (2, "HYBRID"), (3, "HYBRID")])
 def test_integer_bit_exact(ta, tb, levels, variant):
     m, n, k = 301, 263, 418
     A, B = stored(m, n, k, ta, tb, W.integer, 10)

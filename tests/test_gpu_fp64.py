@@ -31,7 +31,7 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["ABC", "AB", "NAIVE"]
+VARIANTS = ["ABC", "AB", "NAIVE", "HYBRID"]
 TOL = {0: 1e-13, 1: 1e-13, 2: 1e-12, 3: 1e-12}
 U = 2.0 ** -53
 
