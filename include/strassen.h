@@ -348,8 +348,10 @@ STRASSEN_API double strassen_model_seconds(int64_t m, int64_t n, int64_t k, int 
  *                        T = log2 measured seconds - the model's log2 seconds.
  * strassen_mlp_adam      one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1)
  *                        on `count` parameters with moment buffers m, v (DEVICE).
- * strassen_selector_load copies a trained parameter vector (HOST) to the current device
- *                        and makes strassen_select() use it; strassen_selector_clear
+ * strassen_selector_load keeps a copy of a trained parameter vector (HOST) and makes
+ *                        strassen_select() use it on every device: the current device
+ *                        gets its device copy at once, any other device on its first
+ *                        selection (outside a stream capture); strassen_selector_clear
  *                        forgets it (and re-enables every dtype).
  * strassen_selector_use  enables (1) or disables (0) the network for one dtype
  *                        (default: all enabled); with it disabled, strassen_select()

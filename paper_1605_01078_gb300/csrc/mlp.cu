@@ -20,6 +20,7 @@
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "internal.h"
 
@@ -174,12 +175,42 @@ struct ShapeKeyHash {
 };
 
 std::mutex g_mlp_mu;
-float* g_sel_params = nullptr;  // device copy of the loaded network (on the loader's device)
-int* g_sel_out = nullptr;
-cudaStream_t g_sel_stream = nullptr;
-int g_sel_device = -1;
+// The loaded network: a host copy, and per device a copy of it (made on the device's
+// first selection), the result word and a private stream.
+std::vector<float> g_sel_host;
+unsigned g_sel_version = 0;  // bumped by every load; device copies of an older version are refreshed
+struct SelDevice {
+  float* params = nullptr;
+  int* out = nullptr;
+  cudaStream_t stream = nullptr;
+  unsigned version = 0;
+};
+constexpr int kSelMaxDevices = 64;
+SelDevice g_sel_dev[kSelMaxDevices];
 unsigned g_sel_dtypes = 0x7u;  // bit d: use the network for dtype d
-std::unordered_map<ShapeKey, int, ShapeKeyHash> g_sel_cache;  // choices of the loaded network
+std::unordered_map<ShapeKey, int, ShapeKeyHash> g_sel_cache[kSelMaxDevices];  // choices per device
+
+// The current device's copy of the network, made or refreshed if needed (may allocate
+// and copy); null on failure.
+SelDevice* sel_device(int dev) {
+  SelDevice& sd = g_sel_dev[dev];
+  if (!sd.params) {
+    if (cudaMalloc(&sd.params, sizeof(float) * kParams) != cudaSuccess || cudaMalloc(&sd.out, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sd.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    sd.version = 0;
+  }
+  if (sd.version != g_sel_version) {
+    if (cudaMemcpy(sd.params, g_sel_host.data(), sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    sd.version = g_sel_version;
+  }
+  return &sd;
+}
 
 int grid_for_batch(int batch) { return batch < 1 ? 1 : (batch < 1024 ? batch : 1024); }
 
@@ -231,34 +262,37 @@ void selector_features(int64_t m, int64_t n, int64_t k, int dtype, float* x, flo
 
 bool mlp_select(int64_t m, int64_t n, int64_t k, int dtype, int may_launch, int* candidate) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
-  if (!g_sel_params || dtype < 0 || dtype > 2 || !((g_sel_dtypes >> dtype) & 1u)) return false;
+  if (g_sel_host.empty() || dtype < 0 || dtype > 2 || !((g_sel_dtypes >> dtype) & 1u)) return false;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev != g_sel_device) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSelMaxDevices) {
     cudaGetLastError();
     return false;
   }
   const ShapeKey key{m, n, k, dtype};
-  auto it = g_sel_cache.find(key);
-  if (it != g_sel_cache.end()) {
+  auto& cache = g_sel_cache[dev];
+  auto it = cache.find(key);
+  if (it != cache.end()) {
     *candidate = it->second;
     return true;
   }
   if (!may_launch) return false;
+  SelDevice* sd = sel_device(dev);
+  if (!sd) return false;
   SelectArgs a;
   selector_features(m, n, k, dtype, a.x, a.base);
   a.valid = 0;
   for (int c = 0; c < kOut; ++c)
     if (selector_candidate_valid(c, dtype)) a.valid |= 1u << c;
-  mlp_select_kernel<<<1, kBlock, 0, g_sel_stream>>>(g_sel_params, a, g_sel_out);
+  mlp_select_kernel<<<1, kBlock, 0, sd->stream>>>(sd->params, a, sd->out);
   int host = -1;
-  if (cudaMemcpyAsync(&host, g_sel_out, sizeof(int), cudaMemcpyDeviceToHost, g_sel_stream) != cudaSuccess ||
-      cudaStreamSynchronize(g_sel_stream) != cudaSuccess) {
+  if (cudaMemcpyAsync(&host, sd->out, sizeof(int), cudaMemcpyDeviceToHost, sd->stream) != cudaSuccess ||
+      cudaStreamSynchronize(sd->stream) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   if (host < 0 || host >= kOut) return false;
-  if (g_sel_cache.size() > 100000) g_sel_cache.clear();
-  g_sel_cache[key] = host;
+  if (cache.size() > 100000) cache.clear();
+  cache[key] = host;
   *candidate = host;
   return true;
 }
@@ -303,24 +337,20 @@ int strassen_mlp_adam(float* params, const float* grad, float* m, float* v, int 
 int strassen_selector_load(const float* params_host, int count) {
   if (count != kParams) return STRASSEN_ERR_ARG;
   if (!params_host) return STRASSEN_ERR_NULL;
-  std::lock_guard<std::mutex> lock(g_mlp_mu);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return STRASSEN_ERR_CUDA;
-  if (!g_sel_params) {
-    if (cudaMalloc(&g_sel_params, sizeof(float) * kParams) != cudaSuccess ||
-        cudaMalloc(&g_sel_out, sizeof(int)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&g_sel_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  try {
+    std::lock_guard<std::mutex> lock(g_mlp_mu);
+    g_sel_host.assign(params_host, params_host + kParams);
+    ++g_sel_version;
+    for (auto& c : g_sel_cache) c.clear();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSelMaxDevices) {
       cudaGetLastError();
-      return STRASSEN_ERR_ALLOC;
+      return STRASSEN_ERR_CUDA;
     }
-    g_sel_device = dev;
-  } else if (dev != g_sel_device) {
-    return STRASSEN_ERR_ARG;
+    return sel_device(dev) ? STRASSEN_OK : STRASSEN_ERR_ALLOC;
+  } catch (...) {
+    return STRASSEN_ERR_ALLOC;
   }
-  if (cudaMemcpy(g_sel_params, params_host, sizeof(float) * kParams, cudaMemcpyHostToDevice) != cudaSuccess)
-    return STRASSEN_ERR_CUDA;
-  g_sel_cache.clear();
-  return STRASSEN_OK;
 }
 
 int strassen_selector_use(int dtype, int enable) {
@@ -328,7 +358,7 @@ int strassen_selector_use(int dtype, int enable) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
   if (enable) g_sel_dtypes |= 1u << dtype;
   else g_sel_dtypes &= ~(1u << dtype);
-  g_sel_cache.clear();
+  for (auto& c : g_sel_cache) c.clear();
   return STRASSEN_OK;
 }
 
@@ -361,18 +391,24 @@ int strassen_selector_features(int64_t m, int64_t n, int64_t k, strassen_dtype d
 
 int strassen_selector_clear(void) {
   std::lock_guard<std::mutex> lock(g_mlp_mu);
-  if (g_sel_params) {
-    cudaStreamSynchronize(g_sel_stream);
-    cudaFree(g_sel_params);
-    cudaFree(g_sel_out);
-    cudaStreamDestroy(g_sel_stream);
-    g_sel_params = nullptr;
-    g_sel_out = nullptr;
-    g_sel_stream = nullptr;
-    g_sel_device = -1;
+  int cur = 0;
+  const bool have_cur = cudaGetDevice(&cur) == cudaSuccess;
+  for (int d = 0; d < kSelMaxDevices; ++d) {
+    SelDevice& sd = g_sel_dev[d];
+    if (!sd.params) continue;
+    if (cudaSetDevice(d) == cudaSuccess) {
+      cudaStreamSynchronize(sd.stream);
+      cudaFree(sd.params);
+      cudaFree(sd.out);
+      cudaStreamDestroy(sd.stream);
+    }
+    sd = SelDevice();
   }
+  if (have_cur) cudaSetDevice(cur);
+  cudaGetLastError();
+  g_sel_host.clear();
   g_sel_dtypes = 0x7u;
-  g_sel_cache.clear();
+  for (auto& c : g_sel_cache) c.clear();
   return STRASSEN_OK;
 }
 
