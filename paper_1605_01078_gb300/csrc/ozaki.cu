@@ -14,9 +14,10 @@
 //   2. slice products (oz_gemm, tcgen05 + TMEM): for every weight w = s + t <= 8 (28
 //      digit pairs) the exact integer G_w = sum_{s+t=w} D_s^X D_t^V.  BF16 x BF16
 //      products of digits (|.| <= 2^14) are exact in FP32 and every FP32 accumulation
-//      chunk holds at most 256 of them (|sum| <= 2^22), so the tensor-core accumulator
-//      stays exact; the epilogue warps convert each chunk to int32 and sum the chunks of
-//      a weight (at most 16384 k per segment keeps the sum below 2^31);
+//      chunk holds at most 1024 of them (every partial sum an integer of magnitude at
+//      most 2^24, representable in FP32), so the tensor-core accumulator stays exact;
+//      the epilogue warps convert each chunk to int32 and sum the chunks of a weight
+//      (at most 16384 k per segment keeps the sum below 2^31);
 //   3. recombine + scatter (oz_recombine_local up to two levels, oz_recombine_scatter
 //      at three): T = sum_w G_w 2^(8(8-w)) exactly in
 //      128-bit integers (Horner over w, segments added), M = RN(T) 2^(e_i + f_j - 64)
@@ -28,10 +29,14 @@
 // split and recombine steps use integer arithmetic for everything but the operand sums
 // and the final C additions (digits are converted from 32-bit integers: a 64-bit
 // integer conversion would run on the FP64 pipe); the products run on the BF16 tensor cores (tcgen05.mma
-// kind::f16, 128x256 tiles, accumulators in tensor memory) fed by TMA with 128-byte
-// swizzle.  The 128x256 tile moves 3/4 of the operand bytes per flop of a 128x128 one
-// (the 128x128 kernel was held by L2-to-SM bandwidth); int32 chunk sums keep its
-// 128 x 256 accumulator set in the epilogue warps' registers.  INT8 slices are not
+// kind::f16, accumulators in tensor memory) fed by TMA with 128-byte swizzle.  One CTA
+// pair (cta_group::2) computes a 256 x 256 tile: each SM stages 128 rows of A's and 128
+// rows of B's digit tile, 32 KB per k-block of 64, where a lone CTA with a 128 x 256
+// tile needs 48 KB for the same products (at the full tensor rate more than the ~60 B
+// per clock an SM received from the L2 in that kernel).  Every chunk drains the whole
+// accumulator through tcgen05.ld: with chunks of 256 products the drains held the tensor
+// pipe near two thirds busy, with 1024 they cost a few percent.  int32 chunk sums keep
+// each CTA's 128 x 256 accumulator set in the epilogue warps' registers.  INT8 slices are not
 // used: the INT8 tensor rate of this part (measured 150 TOP/s) is far below its BF16
 // rate (1950 TFLOP/s).
 #include <cuda.h>
@@ -54,13 +59,17 @@ __device__ int g_oz_status;
 constexpr int kS = 7;          // digits per operand
 constexpr int kB = 8;          // bits per digit: |d| <= 128, exact in BF16
 constexpr int kGroups = kS;    // weights w = s + t = 2 .. kS + 1
-constexpr int kTM = 128, kTN = 256, kTK = 64;  // tile; kTK bf16 = one 128-byte row
-constexpr int kStages = 4;
-constexpr int kChunkItems = 4;   // k-blocks of 64 per exact FP32 chunk: 256 products, |sum| <= 2^22
+// A CTA pair (a cluster of two CTAs, tcgen05 cta_group::2) computes one kPairM x kTN
+// tile: each CTA stages kTM rows of the A digit tile and kHalfN rows of the B digit tile
+// and holds kTM x kTN of the accumulator in its tensor memory.
+constexpr int kTM = 128, kPairM = 256, kTN = 256, kHalfN = 128, kTK = 64;  // kTK bf16 = one 128-byte row
+constexpr int kStages = 6;
+constexpr int kStageBytes = (kTM + kHalfN) * 128;  // one CTA's share of a k-block
+constexpr int kChunkItems = 16;  // k-blocks of 64 per exact FP32 chunk: 1024 products, |sum| <= 2^24
 constexpr int kSegKB = 256;      // k-blocks per k segment: int32 group sums stay below 2^31
-constexpr int kGroupRows = 16;   // tile rows per group of the unit order (L2 reuse)
+constexpr int kGroupRows = 8;    // pair-tile rows per group of the unit order (L2 reuse)
 constexpr int kThreads = 384;    // warp 0 TMA, warp 1 MMA + TMEM, warps 4..11 epilogue
-constexpr int kEpiThreads = 256;
+constexpr int kEpiThreads = 256, kEpiWarps = kEpiThreads / 32;
 constexpr long long kWaitLimit = 2000000000LL;
 constexpr int kLaunchRegs = 168, kLowRegs = 40, kHighRegs = 232;
 static_assert(128 * kLowRegs + 256 * kHighRegs == kThreads * kLaunchRegs, "register split");
@@ -306,10 +315,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
+// Arrival on the barrier at shared::cluster address `addr` (this CTA's or the peer's).
+// The default CTA-scope release suffices: the only accesses it orders across the pair
+// are tensor-memory reads, which tcgen05.fence::before_thread_sync orders before it (a
+// cluster-scope release would also wait for the thread's earlier global stores).
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];\n" ::"r"(addr) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
@@ -322,11 +339,37 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (clock64() - t0 > kWaitLimit) return false;
   return true;
 }
-__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_index() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_total() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;\n" : "=r"(r));
+  return r;
+}
+// shared::cluster address of this CTA's variable `p` in the cluster CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// TMA tile load into this CTA's shared memory whose completion is counted on the
+// barrier at shared::cluster address `bar` (the leading CTA's barrier of the pair).
+__device__ __forceinline__ void tma_2d_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
 // Shared-memory matrix descriptor: K-major operand tile with 128-byte swizzle, rows of
@@ -335,29 +378,44 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M = N = 128.
+// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, M = 256
+// (rows 0-127 from the even CTA of the pair, 128-255 from the odd one), N = 256 (B rows
+// 0-127 staged by the even CTA, 128-255 by the odd one).
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTN >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
+                            ((uint32_t)(kPairM >> 4) << 24);
 
+// One pair MMA (issued by the even CTA): D[tmem of both CTAs] (+)= A B^T over K = 16.
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
       : "memory");
 }
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+// Arrival, once the MMAs issued so far complete, on the barrier at this offset in both CTAs.
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+// The same on this CTA's barrier only.
+__device__ __forceinline__ void umma_commit_local(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
                : "memory");
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr)
       : "memory");
 }
@@ -379,57 +437,65 @@ __host__ __device__ constexpr int pairs_of(int w) {
   return (w - 1 < kS ? w - 1 : kS) - (w - kS > 1 ? w - kS : 1) + 1;
 }
 
-// Exact conversion of an FP32 integer value |v| <= 2^22 to int32: adding 1.5 * 2^23
-// puts v's integer bits in the low mantissa bits of a number in [2^23, 2^24].
-__device__ __forceinline__ int f32_int_exact(uint32_t bits) {
-  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
+// Conversion of an FP32 chunk value (an integer, |v| <= 2^24) to int32: exact.  (Adding
+// 1.5 * 2^23 and taking the bit pattern, one FADD, is exact only for |v| <= 2^22, which
+// would cap a chunk at 256 products and drain the accumulator four times as often.)
+__device__ __forceinline__ uint32_t f32_int(uint32_t bits) { return (uint32_t)__float2int_rz(__uint_as_float(bits)); }
 
-// Work unit u = (product p, tile t, k segment g): a 128 x 256 block of every G_w of
+// Work unit u = (product p, pair tile t, k segment g): a 256 x 256 block of every G_w of
 // product p over the k-blocks of segment g (stored per segment; the recombination adds
-// the segments).  Warp 0 issues TMA loads of digit tiles
-// into a 4-stage ring, warp 1 issues tcgen05.mma (M = 128, N = 256, K = 16) into a
-// double-buffered FP32 accumulator in tensor memory (2 x 256 columns), and eight
-// epilogue warps turn every chunk of at most 256 digit products (|sum| <= 2^22, exact in
-// FP32) into int32 and sum the chunks of a weight w in registers; at the end of each
-// weight the exact G_w tile goes to global memory.
-__global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ GemmArgs a) {
+// the segments), computed by one CTA pair (a cluster of two CTAs).  In each CTA warp 0
+// issues TMA loads of the CTA's 128 rows of the A digit tile and 128 rows of the B digit
+// tile into a 6-stage ring, counted on the even CTA's barrier; the even CTA's warp 1
+// issues tcgen05.mma (cta_group::2, M = 256, N = 256, K = 16) into a double-buffered FP32
+// accumulator (2 x 256 columns of each CTA's tensor memory: rows 0-127 in the even CTA,
+// 128-255 in the odd one) and signals both CTAs; in each CTA eight epilogue warps turn
+// every chunk of at most 1024 digit products (|sum| <= 2^24, exact in FP32) into int32
+// and sum the chunks of a weight w in registers; at the end of each weight the exact G_w
+// rows of the CTA go to global memory.  Each SM receives 32 KB of operands per 128 x 256
+// x 64 share of the products, two thirds of what one CTA computing a 128 x 256 tile
+// alone must load.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ GemmArgs a) {
   extern __shared__ __align__(1024) uint8_t sm_raw[];
-  // 1024-byte aligned stage ring for the 128-byte swizzle
+  // 1024-byte aligned stage ring for the 128-byte swizzle (the same offsets in both CTAs)
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* stA = sm;                               // [kStages][128 rows][128 B]
-  uint8_t* stB = sm + kStages * kTM * 128;         // [kStages][256 rows][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(stB + kStages * kTN * 128);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kStages;
-  uint64_t* tfull = bars + 2 * kStages;
-  uint64_t* tempty = bars + 2 * kStages + 2;
+  uint8_t* stB = sm + kStages * kTM * 128;         // [kStages][128 rows][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stB + kStages * kHalfN * 128);
+  uint64_t* full = bars;                   // even CTA: both CTAs' loads of a stage landed
+  uint64_t* empty = bars + kStages;        // both CTAs: the MMAs reading a stage completed
+  uint64_t* tfull = bars + 2 * kStages;    // both CTAs: an accumulator buffer is complete
+  uint64_t* tempty = bars + 2 * kStages + 2;  // even CTA: both CTAs' epilogues read a buffer
   uint64_t* drain = bars + 2 * kStages + 4;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
 
+  const uint32_t rank = cluster_ctarank();  // 0: issues the MMAs of the pair
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-    for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], kEpiThreads); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 2 * kEpiWarps); }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(tmem_slot))
+    // collective over the pair: the same 512 columns in both CTAs
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(tmem_slot))
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    tc_fence_before();
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n" ::: "memory");
   }
+  tc_fence_before();
   __syncthreads();
+  cluster_sync();  // both CTAs' barriers initialised and tensor memory allocated
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
   const int tiles = a.tiles_m * a.tiles_n;
   const int units = a.P * tiles * a.nseg;
-  // Unit u -> (product, tile, k segment).  Within a product the tiles go in groups of
-  // kGroupRows tile rows, column by column inside a group, so that the units running at
-  // the same time share their A digit rows and B digit columns in the L2.
+  const int u_first = (int)cluster_index(), u_step = (int)cluster_total();
+  // Unit u -> (product, pair tile, k segment).  Within a product the tiles go in groups
+  // of kGroupRows tile rows, column by column inside a group, so that the units running
+  // at the same time share their A digit rows and B digit columns in the L2.
   auto unit_of = [&](int u, int* p, int* tm, int* tn, int* kb0, int* kb1) {
     const int per_p = tiles * a.nseg;
     *p = u / per_p;
@@ -448,25 +514,26 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
   if (warp < 4) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kLowRegs));
     if (warp == 0 && lane == 0) {
-      // ------------------------------------------------ TMA producer
+      // ------------------------------------------------ TMA producer (both CTAs)
+      const uint32_t full0 = cluster_addr(full, 0);
       uint32_t it = 0;
       bool bad = false;
-      for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+      for (int u = u_first; u < units && !bad; u += u_step) {
         int p, tm, tn, kb0, kb1;
         unit_of(u, &p, &tm, &tn, &kb0, &kb1);
         for (int w = 2; w <= kS + 1 && !bad; ++w) {
           const int s_lo = w - kS > 1 ? w - kS : 1, s_hi = w - 1 < kS ? w - 1 : kS;
           for (int s = s_lo; s <= s_hi && !bad; ++s) {
             const int tt = w - s;
-            const int ya = (int)(((int64_t)p * kS + (s - 1)) * a.h_mp + (int64_t)tm * kTM);
-            const int yb = (int)(((int64_t)p * kS + (tt - 1)) * a.h_np + (int64_t)tn * kTN);
+            const int ya = (int)(((int64_t)p * kS + (s - 1)) * a.h_mp + (int64_t)tm * kPairM + kTM * rank);
+            const int yb = (int)(((int64_t)p * kS + (tt - 1)) * a.h_np + (int64_t)tn * kTN + kHalfN * rank);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = it % kStages;
               const uint32_t use = it / kStages;
               if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) { bad = true; break; }
-              mbar_expect_tx(&full[st], (kTM + kTN) * 128);
-              tma_2d(stA + st * kTM * 128, &a.tmA, kb * kTK, ya, &full[st]);
-              tma_2d(stB + st * kTN * 128, &a.tmB, kb * kTK, yb, &full[st]);
+              if (rank == 0) mbar_expect_tx(&full[st], 2 * kStageBytes);
+              tma_2d_pair(stA + st * kTM * 128, &a.tmA, kb * kTK, ya, full0 + 8u * st);
+              tma_2d_pair(stB + st * kHalfN * 128, &a.tmB, kb * kTK, yb, full0 + 8u * st);
             }
           }
         }
@@ -476,11 +543,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
         const long long t0 = clock64();  // let copies in flight land before leaving
         while (clock64() - t0 < 2000000) {}
       }
-    } else if (warp == 1 && lane == 0) {
-      // ------------------------------------------------ MMA issuer
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+      // ------------------------------------------------ MMA issuer (even CTA)
       uint32_t it = 0, ch = 0;
       bool bad = false;
-      for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+      for (int u = u_first; u < units && !bad; u += u_step) {
         int p, tm, tn, kb0, kb1;
         unit_of(u, &p, &tm, &tn, &kb0, &kb1);
         for (int w = 2; w <= kS + 1 && !bad; ++w) {
@@ -496,18 +563,18 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
               if (!mbar_wait(&full[st], (it / kStages) & 1)) { bad = true; break; }
               tc_fence_after();
               const uint64_t ad = sw128_desc(smem_u32(stA + st * kTM * 128));
-              const uint64_t bd = sw128_desc(smem_u32(stB + st * kTN * 128));
+              const uint64_t bd = sw128_desc(smem_u32(stB + st * kHalfN * 128));
 #pragma unroll
               for (int k = 0; k < kTK / 16; ++k)
                 umma(tmem + buf * kTN, ad + 2 * k, bd + 2 * k, (i > c0 || k > 0) ? 1u : 0u);
-              umma_commit(&empty[st]);
+              umma_commit_pair(&empty[st]);
             }
-            umma_commit(&tfull[buf]);
+            umma_commit_pair(&tfull[buf]);
           }
         }
       }
-      // Wait (bounded) until every issued MMA has completed before TMEM is released.
-      umma_commit(drain);
+      // Wait (bounded) until every issued MMA has completed before tensor memory is released.
+      umma_commit_local(drain);
       mbar_wait(drain, 0);
       if (bad) {
         atomicExch(&g_oz_status, STRASSEN_ERR_TIMEOUT);
@@ -515,17 +582,18 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(kHighRegs));
-    // ------------------------------------------------ epilogue warps
+    // ------------------------------------------------ epilogue warps (both CTAs)
     const int ew = warp - 4;
     const int g = warp & 3;         // TMEM lane quarter this warp may read
     const int half = ew >> 2;       // column half (128 columns) of the tile
+    const uint32_t tempty0 = cluster_addr(tempty, 0);
     uint32_t ch = 0;
     bool bad = false;
-    int R[128];
-    for (int u = blockIdx.x; u < units && !bad; u += gridDim.x) {
+    uint32_t R[128];  // int32 group sums (unsigned arithmetic: the true sums fit in int32)
+    for (int u = u_first; u < units && !bad; u += u_step) {
       int p, tm, tn, kb0, kb1;
       unit_of(u, &p, &tm, &tn, &kb0, &kb1);
-      const int64_t row = (int64_t)tm * kTM + 32 * g + lane;
+      const int64_t row = (int64_t)tm * kPairM + kTM * rank + 32 * g + lane;
       const int64_t col0 = (int64_t)tn * kTN + 128 * half;
       for (int w = 2; w <= kS + 1 && !bad; ++w) {
 #pragma unroll
@@ -537,32 +605,35 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm(const __grid_constant__ G
           tc_fence_after();
           const uint32_t base = tmem + ((uint32_t)(32 * g) << 16) + buf * kTN + 128 * half;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            uint32_t v[16];
-            tmem_ld16(base + 16 * q, v);
+          for (int q = 0; q < 4; ++q) {  // 32 columns per wait
+            uint32_t v[32];
+            tmem_ld32(base + 32 * q, v);
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 16; ++i) R[16 * q + i] += f32_int_exact(v[i]);
+            for (int i = 0; i < 32; ++i) R[32 * q + i] += f32_int(v[i]);
           }
           tc_fence_before();
-          mbar_arrive(&tempty[buf]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive_cluster(tempty0 + 8u * buf);
         }
         if (bad) break;
         const int seg = kb0 / a.seg_kb;
         int* dst = a.G + ((((int64_t)seg * a.P + p) * kGroups + (w - 2)) * a.h_mp + row) * a.h_np + col0;
         int4* d4 = reinterpret_cast<int4*>(dst);
 #pragma unroll
-        for (int q = 0; q < 32; ++q) d4[q] = make_int4(R[4 * q], R[4 * q + 1], R[4 * q + 2], R[4 * q + 3]);
+        for (int q = 0; q < 32; ++q) d4[q] = make_int4((int)R[4 * q], (int)R[4 * q + 1], (int)R[4 * q + 2], (int)R[4 * q + 3]);
       }
     }
     if (bad) {
       atomicExch(&g_oz_status, STRASSEN_ERR_TIMEOUT);
     }
   }
+  tc_fence_before();
   __syncthreads();
+  cluster_sync();  // nothing of either CTA is still read or written by the other
+  tc_fence_after();
   if (warp == 1) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;\n" ::"r"(tmem) : "memory");
   }
 }
 
@@ -777,7 +848,34 @@ __global__ void __launch_bounds__(256, 3) oz_recombine_local(const __grid_consta
 PFN_cuTensorMapEncodeTiled_v12000 g_oz_encode = nullptr;
 std::once_flag g_oz_once;
 cudaError_t g_oz_init = cudaSuccess;
-size_t oz_gemm_smem() { return (size_t)kStages * (kTM + kTN) * 128 + 1024 + 256; }
+size_t oz_gemm_smem() { return (size_t)kStages * kStageBytes + 1024 + 256; }
+
+// CTA pairs the slice-product grid plans its waves for (two SMs each).
+int pair_slots(int sms) { return std::max(sms / 2, 1); }
+
+// CTA pairs of oz_gemm that can be resident at once on the current device (at most one
+// pair per two SMs; fewer where the SMs of a GPU cluster do not pair up).
+int resident_pairs(int sms) {
+  static std::mutex mu;
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(2 * pair_slots(sms));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = oz_gemm_smem();
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (const void*)oz_gemm, &cfg) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = pair_slots(sms);
+  }
+  n = std::min(n, pair_slots(sms));
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
+}
 
 void oz_init() {
   cudaDriverEntryPointQueryResult q;
@@ -822,9 +920,10 @@ int plan_segments(int64_t units_per_seg, int64_t nkb, int sms) {
 
 int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
   const int64_t P = kPlanCount[levels];
-  const int64_t hmp = round_up(block_edge(m, levels), kTM), hnp = round_up(block_edge(n, levels), kTN),
+  const int64_t hmp = round_up(block_edge(m, levels), kPairM), hnp = round_up(block_edge(n, levels), kTN),
                 hkp = round_up(block_edge(k, levels), kTK);
-  const int64_t nseg = plan_segments(P * (hmp / kTM) * (hnp / kTN), hkp / kTK, std::max(device_sm_count(), 1));
+  const int64_t nseg =
+      plan_segments(P * (hmp / kPairM) * (hnp / kTN), hkp / kTK, pair_slots(std::max(device_sm_count(), 1)));
   const int64_t hk = block_edge(k, levels), hn = block_edge(n, levels);
   const int64_t vsum = levels > 0 ? P * hk * hn * 8 + 256 : 0;  // B operand sums kept between the two B passes
   return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + nseg * kGroups * P * hmp * hnp * 4 + P * hnp * 8 +
@@ -836,8 +935,9 @@ double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels) {
   const int sms = std::max(device_sm_count(), 1);
   const int64_t P = kPlanCount[levels];
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
-  const int64_t hmp = round_up(hm, kTM), hnp = round_up(hn, kTN), hkp = round_up(hk, kTK);
-  const int64_t nseg = plan_segments(P * (hmp / kTM) * (hnp / kTN), hkp / kTK, sms);
+  const int64_t hmp = round_up(hm, kPairM), hnp = round_up(hn, kTN), hkp = round_up(hk, kTK);
+  const int slots = pair_slots(sms);
+  const int64_t nseg = plan_segments(P * (hmp / kPairM) * (hnp / kTN), hkp / kTK, slots);
   int64_t ta = 0, tb = 0, tc = 0;
   for (int r = 0; r < P; ++r) {
     const int row = kPlanOffset[levels] + r;
@@ -848,11 +948,12 @@ double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels) {
   int pairs = 0;
   for (int w = 2; w <= kS + 1; ++w) pairs += pairs_of(w);
   // Slice products at the tensor rate the kernel reaches on large shapes (0.8 of the
-  // BF16 dense peak of about 12.7K flops per clock per SM at 2 GHz), in whole waves.
-  const double units = (double)P * (hmp / kTM) * (hnp / kTN) * nseg;
-  const double waves = std::ceil(units / sms);
-  const double unit_flops = (double)pairs * 2.0 * kTM * kTN * ((double)hkp / nseg);
-  const double t_mma = waves * unit_flops / (0.8 * 12700.0 * 2.0e9);
+  // BF16 dense peak of about 12.7K flops per clock per SM at 2 GHz, two SMs per unit),
+  // in whole waves of CTA pairs.
+  const double units = (double)P * (hmp / kPairM) * (hnp / kTN) * nseg;
+  const double waves = std::ceil(units / slots);
+  const double unit_flops = (double)pairs * 2.0 * kPairM * kTN * ((double)hkp / nseg);
+  const double t_mma = waves * unit_flops / (2.0 * 0.8 * 12700.0 * 2.0e9);
   // HBM passes: operand reads per term (B twice: column maxima, then digits), digit
   // writes and reads, group-sum writes and reads, C read and write.
   const double bytes = 8.0 * (ta * hm * hk + 2.0 * tb * hk * hn) + 2.0 * 2.0 * kS * P * (hmp + hnp) * hkp +
@@ -880,14 +981,14 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   if (sms <= 0) sms = 1;
   const int P = kPlanCount[levels];
   const int64_t hm = block_edge(m, levels), hn = block_edge(n, levels), hk = block_edge(k, levels);
-  const int64_t hmp = round_up(hm, kTM), hnp = round_up(hn, kTN), hkp = round_up(hk, kTK);
+  const int64_t hmp = round_up(hm, kPairM), hnp = round_up(hn, kTN), hkp = round_up(hk, kTK);
   uint8_t* w = (uint8_t*)ws;
   __nv_bfloat16* DX = (__nv_bfloat16*)w;                       w += (size_t)P * kS * hmp * hkp * 2;
   __nv_bfloat16* DV = (__nv_bfloat16*)w;                       w += (size_t)P * kS * hnp * hkp * 2;
   int* ex = (int*)w;                                           w += (size_t)P * hmp * 4;
   int* fx = (int*)w;                                           w += (size_t)P * hnp * 4;
   w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
-  const int nseg = plan_segments((int64_t)P * (hmp / kTM) * (hnp / kTN), hkp / kTK, sms);
+  const int nseg = plan_segments((int64_t)P * (hmp / kPairM) * (hnp / kTN), hkp / kTK, pair_slots(sms));
   int* G = (int*)w;                                            w += (size_t)nseg * kGroups * P * hmp * hnp * 4;
   unsigned long long* colmax = (unsigned long long*)w;  // [P][h_np] magnitude bits
   w += (size_t)P * hnp * 8;
@@ -929,17 +1030,17 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   GemmArgs ga;
   std::memset(&ga, 0, sizeof(ga));
   if (!encode_bf16(&ga.tmA, DX, (int64_t)P * kS * hmp, hkp, kTM) ||
-      !encode_bf16(&ga.tmB, DV, (int64_t)P * kS * hnp, hkp, kTN))
+      !encode_bf16(&ga.tmB, DV, (int64_t)P * kS * hnp, hkp, kHalfN))
     return cudaErrorInvalidValue;
   ga.G = G;
   ga.P = P;
-  ga.tiles_m = (int)(hmp / kTM); ga.tiles_n = (int)(hnp / kTN);
+  ga.tiles_m = (int)(hmp / kPairM); ga.tiles_n = (int)(hnp / kTN);
   ga.nkb = (int)(hkp / kTK);
   ga.nseg = nseg;
   ga.seg_kb = (int)((ga.nkb + nseg - 1) / nseg);
   ga.h_mp = hmp; ga.h_np = hnp;
   const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n * ga.nseg;
-  const int grid = (int)std::min<int64_t>(sms, units);
+  const int grid = 2 * (int)std::min<int64_t>(resident_pairs(sms), units);  // whole CTA pairs
   void* gargs[] = {&ga};
   if (stage_events && (e = cudaEventRecord(stage_events[1], stream)) != cudaSuccess) return e;
   e = cudaLaunchKernel((const void*)oz_gemm, dim3(grid), dim3(kThreads), gargs, oz_gemm_smem(), stream);

@@ -52,6 +52,15 @@ def test_bit_exact_against_the_scheme_oracle(levels, m, n, k):
     assert np.array_equal(got, ref), float(np.max(np.abs(got - ref)))
 
 
+@pytest.mark.parametrize("levels", [0, 1])
+def test_bit_exact_over_several_pair_tiles(levels):
+    """Several 256 x 256 tiles of CTA pairs in both directions, with ragged last rows and
+    columns (h_m = 700 >> levels, h_n = 600 >> levels)."""
+    m, n, k = 700, 600, 520
+    A, B, C = W.uniform(m, k, 21), W.uniform(k, n, 22), W.uniform(m, n, 23)
+    assert np.array_equal(run(A, B, C, levels), ozaki.gemm(A, B, C, levels))
+
+
 @pytest.mark.parametrize("sigma", [4, 10])
 def test_bit_exact_with_spread_exponents(sigma):
     A, B, C = W.scaled(200, 300, 4, sigma), W.scaled(300, 150, 5, sigma), W.scaled(200, 150, 6, sigma)
@@ -98,12 +107,15 @@ def test_int8_slices_not_built():
     assert st == -5
 
 
-def test_extreme_digits_fill_the_exact_chunk_bound():
-    """Every entry 0.5 - 2^-54 (top digit 128): each 256-product FP32 chunk of the
-    top-digit pair sums to exactly 2^22, the largest value the exactness argument
+@pytest.mark.parametrize("k", [512, 1024, 3000])
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_extreme_digits_fill_the_exact_chunk_bound(k, sign):
+    """Every entry 0.5 - 2^-54 (top digit 128): each full 1024-product FP32 chunk of the
+    top-digit pair sums to exactly +-2^24 (k = 1024, 3000), every partial sum an
+    integer within the FP32 exact range, the largest value the exactness argument
     allows; the result must still match the scheme bit for bit."""
     x = 0.5 - 2.0 ** -54
-    A, B = np.full((64, 512), x), np.full((512, 64), -x)
+    A, B = np.full((64, k), x), np.full((k, 64), sign * x)
     C = np.zeros((64, 64))
     ref = ozaki.gemm(A, B, C, 0)
     assert np.array_equal(run(A, B, C, 0), ref)
