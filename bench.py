@@ -364,6 +364,7 @@ def bench_split_precision(sg, W, torch, sizes=(8192, 16384), err_n=8192, reps=3,
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    bf16_sustained = float(peaks.get("bf16_tflops_sustained", bf16))
     out = {"workload": "m=n=k in {8192, 16384} FP64 via BF16 digit slices, A,B,C uniform[-1,1]", "sizes": {}}
     stream = torch.cuda.current_stream()
     for n in sizes:
@@ -374,11 +375,16 @@ def bench_split_precision(sg, W, torch, sizes=(8192, 16384), err_n=8192, reps=3,
             ms = sg.strassen_profile_split_precision(n, n, n, A.data_ptr(), n, B.data_ptr(), n, C.data_ptr(), n, L,
                                                      stream.cuda_stream)
             tf = split_tensor_flops(n, n, n, L) / (ms[1] / 1e3) / 1e12
+            # a slice-product launch of 100 ms or more, one of a run of such calls, runs
+            # under the power cap: its denominator is the sustained peak
+            long_launch = ms[1] >= 100.0
+            peak = bf16_sustained if long_launch else bf16
             row[str(L)] = {"value": 2.0 * n ** 3 / t / 1e9, "unit": UNIT, "ms": t * 1e3,
                            "stage_ms": {"splits": ms[0], "slice_products": ms[1], "recombine_scatter": ms[2]},
-                           "oz_gemm_roofline": {"bound": "tensor", "achieved": tf, "peak": bf16, "unit": "TFLOP/s",
-                                                "frac": tf / bf16,
-                                                "peak_note": "measured BF16 dense peak (burst), MEASURED_PEAKS.json"}}
+                           "oz_gemm_roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                                "frac": tf / peak, "frac_of_burst": tf / bf16,
+                                                "peak_note": "measured BF16 dense peak (%s), MEASURED_PEAKS.json"
+                                                % ("sustained" if long_launch else "burst")}}
         out["sizes"][str(n)] = row
         del A, B, C
         torch.cuda.empty_cache()
