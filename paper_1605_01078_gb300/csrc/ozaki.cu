@@ -71,6 +71,8 @@ constexpr int kGroupRows = 8;    // pair-tile rows per group of the unit order (
 constexpr int kThreads = 384;    // warp 0 TMA, warp 1 MMA + TMEM, warps 4..11 epilogue
 constexpr int kEpiThreads = 256, kEpiWarps = kEpiThreads / 32;
 constexpr long long kWaitLimit = 2000000000LL;
+constexpr int kPaceChunk = 16;          // k-block loads per pacing step
+constexpr long long kPaceLimit = 40000;  // longest pause of one pacing step (clock cycles)
 constexpr int kLaunchRegs = 168, kLowRegs = 40, kHighRegs = 232;
 static_assert(128 * kLowRegs + 256 * kHighRegs == kThreads * kLaunchRegs, "register split");
 
@@ -162,12 +164,16 @@ struct SplitArgs {
                             // term, written by oz_colmax and read by oz_split_cols (null: none)
 };
 
-// One block per output row i of X^ (rows of A's operand sum), product blockIdx.y.
-__global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
+// Blocks are numbered with the product fastest (block b: product b % P, tile b / P), so
+// that the products reading the same rows or columns of A or B run together and all but
+// the first read them from the L2.  `n_products` is P.
+
+// One block per output row i of X^ (rows of A's operand sum) and product.
+__global__ void oz_split_rows(const __grid_constant__ SplitArgs a, int n_products) {
   extern __shared__ unsigned long long rowbuf[];  // h_k binary64 bit patterns
   __shared__ unsigned long long red[32];
-  const int p = blockIdx.y;
-  const int64_t i = blockIdx.x;
+  const int p = (int)(blockIdx.x % (unsigned)n_products);
+  const int64_t i = blockIdx.x / (unsigned)n_products;
   const int row = a.plan_off + p;
   const int nt = c_oz_plans.na[row];
   uint8_t terms[kMaxTerms];
@@ -206,17 +212,18 @@ __global__ void oz_split_rows(const __grid_constant__ SplitArgs a) {
 }
 
 // Column maxima of V^ (B's operand sum) for the per-column scales: one block per 64
-// columns x kColMaxRows rows of the reduction dimension, product blockIdx.z; partial
+// columns x kColMaxRows rows of the reduction dimension and product; partial
 // maxima of the magnitude bits meet in `colmax_bits` (cleared before) by atomicMax
 // (magnitude order equals the order of the bit patterns of non-negative doubles).
 constexpr int kColMaxRows = 256;
 
 __global__ void __launch_bounds__(256) oz_colmax(const __grid_constant__ SplitArgs a,
-                                                 unsigned long long* colmax_bits) {
+                                                 unsigned long long* colmax_bits, int n_products, int col_tiles) {
   __shared__ unsigned long long red[4][64];
-  const int p = blockIdx.z;
-  const int64_t j0 = (int64_t)blockIdx.x * 64;
-  const int64_t kb = (int64_t)blockIdx.y * kColMaxRows;
+  const int p = (int)(blockIdx.x % (unsigned)n_products);
+  const unsigned blk = blockIdx.x / (unsigned)n_products;
+  const int64_t j0 = (int64_t)(blk % (unsigned)col_tiles) * 64;
+  const int64_t kb = (int64_t)(blk / (unsigned)col_tiles) * kColMaxRows;
   const int64_t ke = kb + kColMaxRows < a.h_k ? kb + kColMaxRows : a.h_k;
   const int row = a.plan_off + p;
   const int nt = c_oz_plans.nb[row];
@@ -241,21 +248,24 @@ __global__ void __launch_bounds__(256) oz_colmax(const __grid_constant__ SplitAr
   }
 }
 
-// One block per 64 output columns j x 64 reduction indices k of V^, product blockIdx.z:
-// the digits of the scaled column entries, written transposed ([j][k], k contiguous)
-// through a shared-memory tile.  The block row blockIdx.y == 0 also stores the scale
+// One block per 64 output columns j x 64 reduction indices k of V^ and product: the
+// digits of the scaled column entries, written transposed ([j][k], k contiguous)
+// through a shared-memory tile.  The blocks of the first 64 k also store the scale
 // exponents.
 constexpr int kColTilePitch = 64 + 8;  // bf16 per tile row (padding against bank conflicts)
 constexpr size_t kSplitColsSmem = sizeof(__nv_bfloat16) * kS * 64 * kColTilePitch;
 
 __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ SplitArgs a,
-                                                     const unsigned long long* colmax_bits) {
+                                                     const unsigned long long* colmax_bits, int n_products,
+                                                     int col_tiles) {
   __shared__ int ecol[64];
   extern __shared__ __align__(16) __nv_bfloat16 tile_raw[];  // [kS][64][kColTilePitch]
   auto tile = [&](int s, int c, int k) -> __nv_bfloat16& { return tile_raw[(s * 64 + c) * kColTilePitch + k]; };
-  const int p = blockIdx.z;
-  const int64_t j0 = (int64_t)blockIdx.x * 64;
-  const int64_t k0 = (int64_t)blockIdx.y * 64;
+  const int p = (int)(blockIdx.x % (unsigned)n_products);
+  const unsigned blk = blockIdx.x / (unsigned)n_products;
+  const int64_t j0 = (int64_t)(blk % (unsigned)col_tiles) * 64;
+  const int64_t k_tile = blk / (unsigned)col_tiles;
+  const int64_t k0 = k_tile * 64;
   const int row = a.plan_off + p;
   const int nt = c_oz_plans.nb[row];
   uint8_t terms[kMaxTerms];
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(256) oz_split_cols(const __grid_constant__ Spl
     const int64_t j = j0 + tid;
     const int e = j < a.h_out ? scale_exponent(colmax_bits[(int64_t)p * a.h_outp + j]) : 0;
     ecol[tid] = e;
-    if (blockIdx.y == 0 && j < a.h_outp) a.exps[(int64_t)p * a.h_outp + j] = e;
+    if (k_tile == 0 && j < a.h_outp) a.exps[(int64_t)p * a.h_outp + j] = e;
   }
   __syncthreads();
   const int64_t slice_stride = a.h_outp * a.h_kp;
@@ -430,6 +440,7 @@ struct GemmArgs {
   int nseg;         // k segments of seg_kb <= kSegKB k-blocks (each segment's sums fit in int32)
   int seg_kb;
   int64_t h_mp, h_np;
+  unsigned* pace;   // chunks of loads issued by all CTA pairs in whole waves (zeroed before the launch)
 };
 
 // Number of digit pairs (s, t) with s + t = w, 1 <= s, t <= S.
@@ -516,11 +527,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) oz_gemm
     if (warp == 0 && lane == 0) {
       // ------------------------------------------------ TMA producer (both CTAs)
       const uint32_t full0 = cluster_addr(full, 0);
-      uint32_t it = 0;
+      // Pacing (even CTA): the pairs that run together read the same digit tiles, and
+      // the L2 keeps them only while the pairs stay close along k.  Every kPaceChunk
+      // loads in the whole waves a pair counts itself in a.pace and pauses (at most
+      // kPaceLimit cycles; correctness never depends on it) while it is more than one
+      // step ahead of the average pair.  The last, partial wave is not paced.
+      const int whole_waves_end = (units / u_step) * u_step;
+      const unsigned long long n_pairs = (unsigned long long)u_step;
+      uint32_t it = 0, paced = 0;
       bool bad = false;
       for (int u = u_first; u < units && !bad; u += u_step) {
         int p, tm, tn, kb0, kb1;
         unit_of(u, &p, &tm, &tn, &kb0, &kb1);
+        const bool pace = rank == 0 && u < whole_waves_end;
         for (int w = 2; w <= kS + 1 && !bad; ++w) {
           const int s_lo = w - kS > 1 ? w - kS : 1, s_hi = w - 1 < kS ? w - 1 : kS;
           for (int s = s_lo; s <= s_hi && !bad; ++s) {
@@ -530,6 +549,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) oz_gemm
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
               const int st = it % kStages;
               const uint32_t use = it / kStages;
+              if (pace && (it % kPaceChunk) == 0) {
+                ++paced;
+                unsigned total = atomicAdd(a.pace, 1u) + 1u;
+                const long long t0 = clock64();
+                while ((unsigned long long)(paced - 1) * n_pairs > (unsigned long long)total &&
+                       clock64() - t0 < kPaceLimit) {
+                  __nanosleep(128);
+                  total = *reinterpret_cast<volatile unsigned*>(a.pace);
+                }
+              }
               if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) { bad = true; break; }
               if (rank == 0) mbar_expect_tx(&full[st], 2 * kStageBytes);
               tma_2d_pair(stA + st * kTM * 128, &a.tmA, kb * kTK, ya, full0 + 8u * st);
@@ -927,7 +956,7 @@ int64_t ozaki_workspace_bytes(int64_t m, int64_t n, int64_t k, int levels) {
   const int64_t hk = block_edge(k, levels), hn = block_edge(n, levels);
   const int64_t vsum = levels > 0 ? P * hk * hn * 8 + 256 : 0;  // B operand sums kept between the two B passes
   return P * kS * (hmp + hnp) * hkp * 2 + P * (hmp + hnp) * 4 + nseg * kGroups * P * hmp * hnp * 4 + P * hnp * 8 +
-         vsum + 4096;
+         256 + vsum + 4096;
 }
 
 double ozaki_model_seconds(int64_t m, int64_t n, int64_t k, int levels) {
@@ -993,6 +1022,8 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   unsigned long long* colmax = (unsigned long long*)w;  // [P][h_np] magnitude bits
   w += (size_t)P * hnp * 8;
   w = (uint8_t*)(((uintptr_t)w + 255) & ~(uintptr_t)255);
+  unsigned* pace = (unsigned*)w;  // the slice-product kernel's pacing counter
+  w += 256;
   unsigned long long* vsum = levels > 0 ? (unsigned long long*)w : nullptr;  // [P][h_k][h_n]
 
   SplitArgs sa;
@@ -1007,7 +1038,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
     if (e != cudaSuccess) return e;
   }
   if (stage_events && cudaEventRecord(stage_events[0], stream) != cudaSuccess) return cudaGetLastError();
-  oz_split_rows<<<dim3((unsigned)hmp, (unsigned)P), 256, row_smem, stream>>>(sa);
+  oz_split_rows<<<(unsigned)(hmp * P), 256, row_smem, stream>>>(sa, P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
@@ -1018,12 +1049,12 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   sb.vsum = vsum;
   e = cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * (size_t)P * hnp, stream);
   if (e != cudaSuccess) return e;
-  oz_colmax<<<dim3((unsigned)(hnp / 64), (unsigned)((hk + kColMaxRows - 1) / kColMaxRows), (unsigned)P), 256, 0,
-              stream>>>(sb, colmax);
+  oz_colmax<<<(unsigned)((hnp / 64) * ((hk + kColMaxRows - 1) / kColMaxRows) * P), 256, 0, stream>>>(
+      sb, colmax, P, (int)(hnp / 64));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  oz_split_cols<<<dim3((unsigned)(hnp / 64), (unsigned)(hkp / 64), (unsigned)P), 256, kSplitColsSmem, stream>>>(
-      sb, colmax);
+  oz_split_cols<<<(unsigned)((hnp / 64) * (hkp / 64) * P), 256, kSplitColsSmem, stream>>>(sb, colmax, P,
+                                                                                           (int)(hnp / 64));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
 
@@ -1039,8 +1070,10 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   ga.nseg = nseg;
   ga.seg_kb = (int)((ga.nkb + nseg - 1) / nseg);
   ga.h_mp = hmp; ga.h_np = hnp;
+  ga.pace = pace;
   const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n * ga.nseg;
   const int grid = 2 * (int)std::min<int64_t>(resident_pairs(sms), units);  // whole CTA pairs
+  if ((e = cudaMemsetAsync(pace, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
   void* gargs[] = {&ga};
   if (stage_events && (e = cudaEventRecord(stage_events[1], stream)) != cudaSuccess) return e;
   e = cudaLaunchKernel((const void*)oz_gemm, dim3(grid), dim3(kThreads), gargs, oz_gemm_smem(), stream);
