@@ -289,12 +289,23 @@ def save_rows(path: str, rows) -> None:
         json.dump(rows, fh)
 
 
-def load_rows(path: str):
-    """Timed rows from a JSON list, or from a file of one JSON row per line (.jsonl)."""
-    with open(path) as fh:
-        if path.endswith(".jsonl"):
-            return [json.loads(line) for line in fh if line.strip()]
-        return json.load(fh)
+def load_rows(spec: str):
+    """Timed rows from a JSON list, or from a file of one JSON row per line (.jsonl).
+    `spec` is a comma-separated list of such files, each optionally followed by
+    ":f64" or ":oz_bf16" to keep only that dtype's rows (for example the FP64 rows of
+    an earlier run together with freshly timed split-precision rows)."""
+    names = {v: k for k, v in DTYPE_NAME.items()}
+    rows = []
+    for part in spec.split(","):
+        path, _, want = part.partition(":")
+        with open(path) as fh:
+            got = [json.loads(line) for line in fh if line.strip()] if path.endswith(".jsonl") else json.load(fh)
+        if want:
+            if want not in names:
+                raise ValueError("unknown dtype filter %r" % want)
+            got = [r for r in got if r["dtype"] == names[want]]
+        rows += got
+    return rows
 
 
 SWEEP_SQUARE = [2048 * i for i in range(1, 9)]
@@ -373,8 +384,9 @@ def main(argv=None) -> int:
     ap.add_argument("--out", required=True)
     ap.add_argument("--sweep", action="store_true", help="run the FP64 shape sweep only")
     ap.add_argument("--measure-only", action="store_true", help="time the shapes and save the rows; no training")
-    ap.add_argument("--train-rows", default=None, help="timed training rows saved by an earlier run (JSON)")
-    ap.add_argument("--heldout-rows", default=None, help="timed held-out rows saved by an earlier run (JSON)")
+    ap.add_argument("--train-rows", default=None,
+                    help="timed training rows saved by earlier runs: file[:dtype][,file[:dtype]...] (JSON)")
+    ap.add_argument("--heldout-rows", default=None, help="timed held-out rows, as --train-rows")
     ap.add_argument("--train-skip", type=int, default=0,
                     help="skip the first N FP64 training shapes (already timed), time the rest of --train")
     ap.add_argument("--oz-train-skip", type=int, default=0, help="the same for the split-precision training shapes")
