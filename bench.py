@@ -528,6 +528,10 @@ def main():
     m = n = k = args.n
     L, variant = args.levels, args.variant
     sg.load_library()
+    # The shipped learned selector, loaded as a user of the package loads it: every
+    # automatic plan below (levels -1, AUTO) is its choice where it is enabled (FP64).
+    from paper_1605_01078_gb300 import tune
+    selector = tune.load_default_selector()
     Ah, Bh, Ch = W.uniform(m, k, 100 + rank), W.uniform(k, n, 200 + rank), W.uniform(m, n, 300 + rank)
     A, B, C = torch.from_numpy(Ah).cuda(), torch.from_numpy(Bh).cuda(), torch.from_numpy(Ch).cuda()
     stream = torch.cuda.current_stream()
@@ -719,6 +723,9 @@ def main():
         "batched": batched,
         "syrk": syrk,
         "split_precision": split,
+        "selector": {"loaded": "shipped network (data/selector_gb300.json)",
+                     "enabled_for": [name for d, name in ((0, "f64"), (2, "oz_bf16"))
+                                     if selector["use_for_dtype"].get(str(d))]},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
