@@ -72,7 +72,7 @@ constexpr int kThreads = 384;    // warp 0 TMA, warp 1 MMA + TMEM, warps 4..11 e
 constexpr int kEpiThreads = 256, kEpiWarps = kEpiThreads / 32;
 constexpr long long kWaitLimit = 2000000000LL;
 constexpr int kPaceChunk = 16;          // k-block loads per pacing step
-constexpr long long kPaceLimit = 40000;  // longest pause of one pacing step (clock cycles)
+constexpr long long kPaceLimit = 10000;  // longest pause of one pacing step (about one step's MMAs)
 constexpr int kLaunchRegs = 168, kLowRegs = 40, kHighRegs = 232;
 static_assert(128 * kLowRegs + 256 * kHighRegs == kThreads * kLaunchRegs, "register split");
 
@@ -440,7 +440,7 @@ struct GemmArgs {
   int nseg;         // k segments of seg_kb <= kSegKB k-blocks (each segment's sums fit in int32)
   int seg_kb;
   int64_t h_mp, h_np;
-  unsigned* pace;   // chunks of loads issued by all CTA pairs in whole waves (zeroed before the launch)
+  unsigned* pace;   // [0] pacing steps counted by the running pairs, [1] running pairs (zeroed before the launch)
 };
 
 // Number of digit pairs (s, t) with s + t = w, 1 <= s, t <= S.
@@ -529,17 +529,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) oz_gemm
       const uint32_t full0 = cluster_addr(full, 0);
       // Pacing (even CTA): the pairs that run together read the same digit tiles, and
       // the L2 keeps them only while the pairs stay close along k.  Every kPaceChunk
-      // loads in the whole waves a pair counts itself in a.pace and pauses (at most
+      // loads in the whole waves a pair counts a step in a.pace[0] and pauses (at most
       // kPaceLimit cycles; correctness never depends on it) while it is more than one
-      // step ahead of the average pair.  The last, partial wave is not paced.
+      // step ahead of the average running pair.  A pair joins at the current average
+      // (one that starts late, its SMs busy with other work, holds nobody back) and on
+      // leaving the whole waves takes its steps out again; the last, partial wave is
+      // not paced.
       const int whole_waves_end = (units / u_step) * u_step;
-      const unsigned long long n_pairs = (unsigned long long)u_step;
+      volatile unsigned* pace_v = a.pace;
       uint32_t it = 0, paced = 0;
+      bool joined = false;
+      if (rank == 0 && u_first < whole_waves_end) {
+        const unsigned before = atomicAdd(&a.pace[1], 1u);
+        paced = before > 0 ? pace_v[0] / before : 0u;
+        atomicAdd(&a.pace[0], paced);
+        joined = true;
+      }
       bool bad = false;
       for (int u = u_first; u < units && !bad; u += u_step) {
         int p, tm, tn, kb0, kb1;
         unit_of(u, &p, &tm, &tn, &kb0, &kb1);
-        const bool pace = rank == 0 && u < whole_waves_end;
+        if (joined && u >= whole_waves_end) {
+          atomicSub(&a.pace[0], paced);
+          atomicSub(&a.pace[1], 1u);
+          joined = false;
+        }
+        const bool pace = joined;
         for (int w = 2; w <= kS + 1 && !bad; ++w) {
           const int s_lo = w - kS > 1 ? w - kS : 1, s_hi = w - 1 < kS ? w - 1 : kS;
           for (int s = s_lo; s <= s_hi && !bad; ++s) {
@@ -551,12 +566,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) oz_gemm
               const uint32_t use = it / kStages;
               if (pace && (it % kPaceChunk) == 0) {
                 ++paced;
-                unsigned total = atomicAdd(a.pace, 1u) + 1u;
+                unsigned total = atomicAdd(&a.pace[0], 1u) + 1u, running = pace_v[1];
                 const long long t0 = clock64();
-                while ((unsigned long long)(paced - 1) * n_pairs > (unsigned long long)total &&
+                while ((unsigned long long)(paced - 1) * running > (unsigned long long)total &&
                        clock64() - t0 < kPaceLimit) {
                   __nanosleep(128);
-                  total = *reinterpret_cast<volatile unsigned*>(a.pace);
+                  total = pace_v[0];
+                  running = pace_v[1];
                 }
               }
               if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) { bad = true; break; }
@@ -566,6 +582,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1) oz_gemm
             }
           }
         }
+      }
+      if (joined) {
+        atomicSub(&a.pace[0], paced);
+        atomicSub(&a.pace[1], 1u);
       }
       if (bad) {
         atomicExch(&g_oz_status, STRASSEN_ERR_TIMEOUT);
@@ -1073,7 +1093,7 @@ cudaError_t run_ozaki(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   ga.pace = pace;
   const int64_t units = (int64_t)P * ga.tiles_m * ga.tiles_n * ga.nseg;
   const int grid = 2 * (int)std::min<int64_t>(resident_pairs(sms), units);  // whole CTA pairs
-  if ((e = cudaMemsetAsync(pace, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(pace, 0, 2 * sizeof(unsigned), stream)) != cudaSuccess) return e;
   void* gargs[] = {&ga};
   if (stage_events && (e = cudaEventRecord(stage_events[1], stream)) != cudaSuccess) return e;
   e = cudaLaunchKernel((const void*)oz_gemm, dim3(grid), dim3(kThreads), gargs, oz_gemm_smem(), stream);
