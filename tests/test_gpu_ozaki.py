@@ -61,6 +61,26 @@ def test_bit_exact_over_several_pair_tiles(levels):
     assert np.array_equal(run(A, B, C, levels), ozaki.gemm(A, B, C, levels))
 
 
+def test_concurrent_with_fp64_work_on_another_stream():
+    """A split-precision call launched while a long FP64 product runs on another stream:
+    its CTA pairs start as SMs free up, so some join the pacing count late; the result is
+    still the scheme's, bit for bit, and the call reports no timeout."""
+    m, n, k = 700, 600, 520
+    A, B, C = W.uniform(m, k, 31), W.uniform(k, n, 32), W.uniform(m, n, 33)
+    ref = ozaki.gemm(A, B, C, 1)
+    big = [W.uniform_device(4096, 4096, s) for s in (34, 35, 36)]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        sg.gemm(big[0], big[1], big[2], levels=2, stream=s1)
+    with torch.cuda.stream(s2):
+        sg.gemm(dA, dB, dC, levels=1, variant="ABC", dtype=OZ, stream=s2)
+    torch.cuda.synchronize()
+    assert sg.strassen_device_status(0) == 0
+    assert np.array_equal(dC.cpu().numpy(), ref)
+
+
 @pytest.mark.parametrize("sigma", [4, 10])
 def test_bit_exact_with_spread_exponents(sigma):
     A, B, C = W.scaled(200, 300, 4, sigma), W.scaled(300, 150, 5, sigma), W.scaled(200, 150, 6, sigma)
