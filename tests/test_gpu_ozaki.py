@@ -109,7 +109,21 @@ def test_fp64_tolerance_config_1024(levels):
     assert oracle.max_rel_err(got, exact, A, B) <= TOL[levels]
 
 
-@pytest.mark.parametrize("levels", [0, 1])
+def test_full_size_classical_slices_bit_exact_on_sampled_entries():
+    """8192^3 classical slices, many waves of CTA pairs: at level 0 an entry of the
+    scheme depends only on its row of A and its column of B (their scales included), so
+    the oracle's product of the sampled rows and columns gives those entries exactly."""
+    n = 8192
+    A, B, C = W.uniform(n, n, 110), W.uniform(n, n, 111), W.uniform(n, n, 112)
+    got = run(A, B, C, 0)
+    rows, cols = W.sample_indices(n, n, 256, 7)
+    R, ri = np.unique(rows, return_inverse=True)
+    Q, qi = np.unique(cols, return_inverse=True)
+    M = ozaki.product(A[R], B[:, Q])
+    assert np.array_equal(got[rows, cols], C[rows, cols] + M[ri, qi])
+
+
+@pytest.mark.parametrize("levels", [0, 1, 2])
 def test_full_size_sampled(levels):
     n = 8192
     A, B, C = W.uniform(n, n, 100), W.uniform(n, n, 101), W.uniform(n, n, 102)
